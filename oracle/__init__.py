@@ -1,0 +1,165 @@
+"""Oracle for the GraphPi pattern-count path.
+
+TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check and the benchmark's
+CPU-baseline leg may import this package. The counting library never imports
+it, and the two share no code: this package reads its inputs from the seeded
+generators in ``synth`` (which hold none of the method's arithmetic) and
+builds its own CSR, automorphism group, restriction sets, schedules and cost
+model from the paper's definitions.
+
+* ``oracle.c`` (plain C11 + pthreads): CSR build, |Aut(P)|, injective map
+  enumeration, restricted enumeration, triangles (Sections II-A, II-B, IV-E).
+* ``planner_ref.py`` (plain Python): automorphisms, Algorithm 1 with
+  ``no_conflict`` and ``validate``, the 2-phase schedule filter and the
+  performance model (Sections IV-A to IV-C).
+
+Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
+(closed forms, brute force over vertex tuples, values the paper prints).
+"""
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+
+
+def build(force=False):
+    """Compile ``oracle.c`` with gcc into ``oracle/_build/liboracle.so``."""
+    src = os.path.join(_HERE, "oracle.c")
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= max(
+            os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
+        return _SO
+    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+    tmp = _SO + f".{os.getpid()}.tmp"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-fPIC", "-shared", "-pthread",
+                           src, "-o", tmp])
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        i32, i64 = ctypes.c_int32, ctypes.c_int64
+        lib.oracle_build_csr.argtypes = [i32, i64, P, P, P, P, P]
+        lib.oracle_aut_count.argtypes = [i32, P, P]
+        lib.oracle_count_maps.argtypes = [i32, P, i32, P, P, i32, i32, i32, i32, P, P]
+        lib.oracle_count.argtypes = [i32, P, i32, P, P, i32, P]
+        lib.oracle_count_restricted.argtypes = [i32, P, P, i32, P, i32, P, P, i32, P, P]
+        lib.oracle_triangles.argtypes = [i32, P, P, i32, P]
+        for f in (lib.oracle_build_csr, lib.oracle_aut_count, lib.oracle_count_maps,
+                  lib.oracle_count, lib.oracle_count_restricted, lib.oracle_triangles):
+            f.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def default_threads():
+    return os.cpu_count() or 1
+
+
+class Csr:
+    """Undirected simple graph in CSR form (int64 row_ptr, int32 col)."""
+
+    def __init__(self, n, row_ptr, col):
+        self.n = int(n)
+        self.row_ptr = row_ptr
+        self.col = col
+
+    @property
+    def nnz(self):
+        return int(self.row_ptr[-1])
+
+
+def build_csr(n, src, dst):
+    src = np.ascontiguousarray(src, dtype=np.int32)
+    dst = np.ascontiguousarray(dst, dtype=np.int32)
+    m = len(src)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    col = np.zeros(max(1, 2 * m), dtype=np.int32)
+    nnz = np.zeros(1, dtype=np.int64)
+    rc = _load().oracle_build_csr(n, m, _p(src), _p(dst), _p(row_ptr), _p(col), _p(nnz))
+    if rc:
+        raise ValueError(f"oracle_build_csr failed ({rc})")
+    return Csr(n, row_ptr, col[: int(nnz[0])].copy())
+
+
+def _adj(adj):
+    adj = np.ascontiguousarray(adj, dtype=np.uint8)
+    if adj.ndim != 2 or adj.shape[0] != adj.shape[1]:
+        raise ValueError("adjacency must be k x k")
+    return adj
+
+
+def aut_count(adj):
+    adj = _adj(adj)
+    out = np.zeros(1, dtype=np.uint64)
+    rc = _load().oracle_aut_count(adj.shape[0], _p(adj), _p(out))
+    if rc:
+        raise ValueError(f"oracle_aut_count failed ({rc})")
+    return int(out[0])
+
+
+def count_maps(adj, g, root_begin=0, root_end=None, root_stride=1, threads=None):
+    """Injective edge-preserving maps (as a Python int) with the image of
+    pattern vertex 0 among the selected roots."""
+    adj = _adj(adj)
+    hi = np.zeros(1, dtype=np.uint64)
+    lo = np.zeros(1, dtype=np.uint64)
+    rc = _load().oracle_count_maps(adj.shape[0], _p(adj), g.n, _p(g.row_ptr), _p(g.col),
+                                   root_begin, g.n if root_end is None else root_end,
+                                   root_stride, threads or default_threads(), _p(hi), _p(lo))
+    if rc:
+        raise ValueError(f"oracle_count_maps failed ({rc})")
+    return (int(hi[0]) << 64) | int(lo[0])
+
+
+def count(adj, g, threads=None):
+    """count(P, G) = maps / |Aut(P)|, as a Python int (may exceed 64 bits)."""
+    maps = count_maps(adj, g, threads=threads)
+    aut = aut_count(adj)
+    if maps % aut:
+        raise AssertionError("map count is not a multiple of |Aut(P)|")
+    return maps // aut
+
+
+def count_restricted(adj, order, restrictions, g, threads=None):
+    """Maps found in matching order ``order`` that obey every restriction
+    ``(a, b)``: id(a) > id(b)."""
+    adj = _adj(adj)
+    k = adj.shape[0]
+    order = np.ascontiguousarray(order, dtype=np.int32)
+    res = np.ascontiguousarray(np.array(restrictions, dtype=np.int32).reshape(-1, 2))
+    if res.size == 0:
+        res = np.zeros((1, 2), dtype=np.int32)
+        nres = 0
+    else:
+        nres = res.shape[0]
+    hi = np.zeros(1, dtype=np.uint64)
+    lo = np.zeros(1, dtype=np.uint64)
+    rc = _load().oracle_count_restricted(k, _p(adj), _p(order), nres, _p(res), g.n,
+                                         _p(g.row_ptr), _p(g.col), threads or default_threads(),
+                                         _p(hi), _p(lo))
+    if rc:
+        raise ValueError(f"oracle_count_restricted failed ({rc})")
+    return (int(hi[0]) << 64) | int(lo[0])
+
+
+def triangles(g, threads=None):
+    """Unordered triangles of the graph."""
+    out = np.zeros(1, dtype=np.uint64)
+    rc = _load().oracle_triangles(g.n, _p(g.row_ptr), _p(g.col), threads or default_threads(), _p(out))
+    if rc:
+        raise ValueError(f"oracle_triangles failed ({rc})")
+    return int(out[0])

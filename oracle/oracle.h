@@ -1,0 +1,77 @@
+/* Oracle for the pattern-count path: plain, slow, obviously correct CPU code.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may call this library. The counting library
+ * never links, loads or calls it, and shares no code with it.
+ *
+ * What it computes (GraphPi, Section II-A, problem definition): a pattern
+ * P = (V_p, E_p) with k vertices matches a data graph G when an injective map
+ * id : V_p -> V sends every pattern edge to a graph edge (non-induced
+ * matching). Maps that differ by an automorphism of P name the same embedding
+ * (Section II-B), so the embedding count is
+ *
+ *     count(P, G) = #{injective edge-preserving maps V_p -> V} / |Aut(P)|.
+ *
+ * The data graph is the undirected simple graph of the input pairs: self loops
+ * dropped, both directions kept, duplicates removed, each neighbour list sorted
+ * ascending (compressed sparse row, Section IV-E).
+ *
+ * All functions return 0 on success and a negative value on bad arguments or
+ * allocation failure.
+ */
+#ifndef GRAPHPI_ORACLE_H
+#define GRAPHPI_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Undirected simple CSR from m sampled pairs over [0, n). row_ptr has n + 1
+ * entries; col must hold 2 * m entries. *nnz receives the directed entry
+ * count (twice the undirected edge count). */
+int oracle_build_csr(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                     int64_t* row_ptr, int32_t* col, int64_t* nnz);
+
+/* |Aut(P)|: permutations p of the k pattern vertices with (p(a), p(b)) in E_p
+ * for every (a, b) in E_p (Section IV-A), by trying all k! permutations.
+ * adj is k * k row-major 0/1. */
+int oracle_aut_count(int32_t k, const uint8_t* adj, uint64_t* out);
+
+/* Number of injective edge-preserving maps of the pattern into the graph
+ * whose image of pattern vertex 0 is one of the roots root_begin,
+ * root_begin + root_stride, ... below root_end (stride 1 = every root). The 128-bit
+ * total is returned in (*hi, *lo). nthreads worker threads split the roots. */
+int oracle_count_maps(int32_t k, const uint8_t* adj,
+                      int32_t n, const int64_t* row_ptr, const int32_t* col,
+                      int32_t root_begin, int32_t root_end, int32_t root_stride,
+                      int32_t nthreads, uint64_t* hi, uint64_t* lo);
+
+/* count(P, G) = maps / |Aut(P)| over all roots. Returns -3 when the maps are
+ * not a multiple of |Aut(P)| (impossible for a correct enumeration) and -4
+ * when the count does not fit in 64 bits. */
+int oracle_count(int32_t k, const uint8_t* adj,
+                 int32_t n, const int64_t* row_ptr, const int32_t* col,
+                 int32_t nthreads, uint64_t* out);
+
+/* Maps enumerated in the given matching order (Section II-B) that also obey
+ * every restriction id(res[2i]) > id(res[2i+1]) (Section II-B). Vertices are
+ * pattern vertex numbers; order is a permutation of 0..k-1. With a correct
+ * restriction set this equals count(P, G) (Algorithm 1, validate). */
+int oracle_count_restricted(int32_t k, const uint8_t* adj, const int32_t* order,
+                            int32_t nres, const int32_t* res,
+                            int32_t n, const int64_t* row_ptr, const int32_t* col,
+                            int32_t nthreads, uint64_t* hi, uint64_t* lo);
+
+/* Unordered triangles {a, b, c} of the graph (the cost model's tri_cnt,
+ * Section IV-C, counts each triangle once per ordered traversal; see the
+ * planner). */
+int oracle_triangles(int32_t n, const int64_t* row_ptr, const int32_t* col,
+                     int32_t nthreads, uint64_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

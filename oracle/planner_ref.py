@@ -1,0 +1,217 @@
+"""Plain restatement of GraphPi's configuration generation and performance
+model (Sections IV-A to IV-C), for checking the library's C++ planner.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+Notation follows the paper. A pattern is a k x k symmetric 0/1 matrix over
+vertices 0..k-1. A permutation ``perm`` is a tuple with ``perm[v]`` the image
+of ``v``. A restriction ``(a, b)`` means id(a) > id(b). A schedule is the
+tuple of pattern vertices in search order; loops are numbered 1..n as in the
+paper's performance model.
+
+Readings of the paper used here (each also listed in the design notes):
+
+* Algorithm 1 tests ``vertex = perm[perm[vertex]]`` to find a 2-cycle; a
+  fixed point also passes that test, so ``perm[vertex] != vertex`` is required
+  too, and the pair added is ``(vertex, perm[vertex])``.
+* ``generate`` depends on its arguments only through ``res_set``: the group
+  it receives is exactly the automorphisms not yet eliminated by
+  ``res_set``, because ``no_conflict`` is monotone (a permutation that closes a
+  cycle under a set still closes it under every superset). Its results are
+  therefore cached per ``res_set``; this changes the running time only.
+* Phase 2 of the schedule filter can leave no schedule at all (for example
+  the 4-cycle and 6-cycle); the largest k' <= k that keeps at least one
+  phase-1 schedule is used instead, and k' = 1 means phase 1 alone.
+* ``|E|`` counts undirected edges; ``tri_cnt`` counts each triangle once per
+  ordered vertex triple (six times per triangle), so that
+  ``|V| p1 p2 = tri_cnt / (2|E|)`` is the mean common-neighbour count of a
+  directed edge, matching the stated meaning of ``p2``.
+* A restriction acts in the loop of its later-scheduled endpoint. ``f_i`` is
+  the fraction of the relative orders still alive at loop i that the
+  restrictions of loop i remove (0 when loop i has none).
+* ``c_i`` sums, over the distinct partial intersections computed in loop i,
+  the estimated sizes of its two operands: the partial set built so far
+  and ``N(v_i)``. A vertex whose candidate set has operands at loops
+  ``j1 < j2 < ... < jm`` gets ``N(v_j1) ∩ N(v_j2)`` in loop j2, that result
+  intersected with ``N(v_j3)`` in loop j3, and so on; equal partial sets
+  (same operand loops) are computed once.
+"""
+
+from functools import lru_cache
+from itertools import combinations, permutations
+from math import factorial
+
+
+def _edges(adj):
+    k = len(adj)
+    return [(a, b) for a in range(k) for b in range(k) if adj[a][b]]
+
+
+def automorphisms(adj):
+    """All permutations preserving the edge set (Section IV-A)."""
+    k = len(adj)
+    E = _edges(adj)
+    return [p for p in permutations(range(k)) if all(adj[p[a]][p[b]] for a, b in E)]
+
+
+def _acyclic(k, arcs):
+    """Kahn's algorithm on a directed graph over 0..k-1."""
+    indeg = [0] * k
+    out = [[] for _ in range(k)]
+    for a, b in arcs:
+        out[a].append(b)
+        indeg[b] += 1
+    ready = [v for v in range(k) if indeg[v] == 0]
+    seen = 0
+    while ready:
+        v = ready.pop()
+        seen += 1
+        for w in out[v]:
+            indeg[w] -= 1
+            if indeg[w] == 0:
+                ready.append(w)
+    return seen == k
+
+
+def no_conflict(perm, res_set):
+    """True when ``perm`` is NOT eliminated by ``res_set``: the digraph with
+    arcs first->second and perm[first]->perm[second] for every restriction is
+    acyclic (Algorithm 1, no_conflict)."""
+    arcs = []
+    for a, b in res_set:
+        arcs.append((a, b))
+        arcs.append((perm[a], perm[b]))
+    return _acyclic(len(perm), arcs)
+
+
+def linear_extensions(k, res_set):
+    """Orderings of k distinct labels obeying every restriction: the
+    restricted embedding count of the pattern in the k-vertex complete graph."""
+    return sum(1 for sigma in permutations(range(k))
+               if all(sigma[a] > sigma[b] for a, b in res_set))
+
+
+def validate(k, aut_count, res_set):
+    """ans_with == ans_without / |Aut| on the k-vertex complete graph, where
+    ans_without = k! (every injective map is an embedding there)."""
+    return linear_extensions(k, res_set) * aut_count == factorial(k)
+
+
+def restriction_sets(adj):
+    """Algorithm 1 (res_set_generation): every restriction set it returns,
+    as a sorted list of sorted tuples of pairs."""
+    k = len(adj)
+    auts = automorphisms(adj)
+    n_aut = len(auts)
+
+    @lru_cache(maxsize=None)
+    def generate(res_set):
+        pg = [p for p in auts if no_conflict(p, res_set)]
+        if len(pg) > 1:
+            sets = set()
+            for perm in pg:
+                for vertex in range(k):
+                    if perm[vertex] != vertex and perm[perm[vertex]] == vertex:  # a 2-cycle
+                        new_set = frozenset(res_set | {(vertex, perm[vertex])})
+                        sets |= generate(new_set)
+            return frozenset(sets)
+        if validate(k, n_aut, res_set):
+            return frozenset([res_set])
+        return frozenset()
+
+    out = generate(frozenset())
+    return sorted(tuple(sorted(s)) for s in out)
+
+
+def max_independent_set_size(adj):
+    k = len(adj)
+    for size in range(k, 0, -1):
+        for sub in combinations(range(k), size):
+            if all(not adj[a][b] for a, b in combinations(sub, 2)):
+                return size
+    return 0
+
+
+def phase1_ok(adj, sched):
+    """Every vertex after the first is adjacent to an earlier one, i.e. every
+    prefix induces a connected subgraph (Section IV-B, phase 1)."""
+    return all(any(adj[sched[i]][sched[j]] for j in range(i)) for i in range(1, len(sched)))
+
+
+def phase2_ok(adj, sched, kk):
+    """The last kk searched vertices are pairwise non-adjacent (phase 2)."""
+    tail = sched[len(sched) - kk:]
+    return all(not adj[a][b] for a, b in combinations(tail, 2))
+
+
+def efficient_schedules(adj):
+    """(schedules, k') : the 2-phase filter with phase 2 relaxed to the
+    largest k' that keeps a schedule."""
+    k = len(adj)
+    p1 = [s for s in permutations(range(k)) if phase1_ok(adj, s)]
+    for kk in range(max_independent_set_size(adj), 0, -1):
+        out = [s for s in p1 if phase2_ok(adj, s, kk)]
+        if out:
+            return out, kk
+    return p1, 1
+
+
+def graph_params(n_vertices, n_edges, tri_cnt):
+    """p1 and p2 of Section IV-C (|E| undirected, tri_cnt ordered)."""
+    V, E = float(n_vertices), float(n_edges)
+    p1 = 2.0 * E / (V * V)
+    p2 = tri_cnt * V / ((2.0 * E) ** 2)
+    return p1, p2
+
+
+def f_values(k, sched, res_set):
+    """f_1..f_n by filtering all k! relative orders loop by loop."""
+    pos = {v: i for i, v in enumerate(sched)}
+    alive = list(permutations(range(k)))
+    f = []
+    for i in range(k):
+        here = [(a, b) for a, b in res_set if max(pos[a], pos[b]) == i]
+        before = len(alive)
+        for a, b in here:
+            alive = [s for s in alive if s[a] > s[b]]
+        f.append(0.0 if not here or before == 0 else (before - len(alive)) / before)
+    return f
+
+
+def cost(adj, sched, res_set, n_vertices, n_edges, tri_cnt):
+    """cost_1 of the nested performance model for one configuration."""
+    k = len(adj)
+    V = float(n_vertices)
+    p1, p2 = graph_params(n_vertices, n_edges, tri_cnt)
+
+    def card(m):                      # m-way intersection of neighbourhoods
+        return V if m == 0 else V * p1 * p2 ** (m - 1)
+
+    ops = [[j for j in range(i) if adj[sched[i]][sched[j]]] for i in range(k)]
+    l = [card(len(ops[i])) for i in range(k)]
+    c = [0.0] * k
+    for i in range(k):
+        built = set()
+        for x in range(i + 1, k):
+            O = ops[x]
+            if i in O and O.index(i) >= 1:
+                prefix = tuple(j for j in O if j <= i)
+                if prefix in built:
+                    continue
+                built.add(prefix)
+                c[i] += card(len(prefix) - 1) + card(1)
+    f = f_values(k, sched, res_set)
+    total = l[k - 1] * (1.0 - f[k - 1])
+    for i in range(k - 2, -1, -1):
+        total = l[i] * (1.0 - f[i]) * (c[i] + total)
+    return total
+
+
+def all_configurations(adj, n_vertices, n_edges, tri_cnt):
+    """Every (cost, schedule, restriction set) over the efficient schedules and
+    Algorithm 1's sets, sorted by cost, then schedule, then set."""
+    scheds, _ = efficient_schedules(adj)
+    sets = restriction_sets(adj)
+    rows = [(cost(adj, s, r, n_vertices, n_edges, tri_cnt), s, r) for s in scheds for r in sets]
+    rows.sort()
+    return rows
