@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""Benchmark: pattern-count time on a device-resident synthetic graph.
+
+One step counts every pattern of the workload once with the plan the
+performance model ranks first (graph build and planning are excluded, as in
+the paper's evaluation; they appear in the end-to-end number instead).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat20]
+  python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+
+With --gpus N > 1 (launched by torch.distributed.run) every rank holds a
+replica of the graph and counts a contiguous share of every pattern's edge
+tasks; the per-rank partial counts are summed across ranks once per step.
+"""
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import named_pattern, workload_edges  # noqa: E402
+
+WORKLOADS = {
+    # R-MAT scale 20, edge factor 16, a/b/c/d .57/.19/.19/.05, seed 2
+    "rmat20": {"graph": "rmat20", "patterns": ["triangle", "k4", "k5", "house", "c6"]},
+    # House on G(2000, 20000), seed 1
+    "er2000": {"graph": "er2000", "patterns": ["house"]},
+    # Chung-Lu 4M vertices, 35M pairs, exponent 2.1, max expected degree 20K, seed 3
+    "cl4m": {"graph": "cl4m", "patterns": ["k6e", "c6chord", "grid3x2"]},
+}
+
+L2_FLUSH_BYTES = 512 << 20          # larger than the 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="rmat20", choices=sorted(WORKLOADS))
+    ap.add_argument("--patterns", default=None, help="comma list overriding the workload's patterns")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU-baseline sample budget")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during timing."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.rows = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", uuid, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = self.rows
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# -------------------------------------------------------------- CPU baseline
+
+def cpu_baseline(n, src, dst, patterns, budget_s):
+    """The oracle (unrestricted enumeration) on a uniform random sample of
+    root vertices; total time is estimated as sample time x (n / sample)."""
+    import oracle
+    threads = os.cpu_count() or 1
+    t0 = time.time()
+    g = oracle.build_csr(n, src, dst)
+    build_s = time.time() - t0
+    rng = np.random.default_rng(12345)
+    per = budget_s / max(1, len(patterns))
+    est, parts, lower = 0.0, [], False
+    for name in patterns:
+        adj = named_pattern(name)
+        stride = max(1, n // 64)
+        done_t, done_roots, finished = 0.0, 0, True
+        # grow the sample (disjoint random offsets of a strided root set) until the budget is used
+        offsets = rng.permutation(stride)
+        for off in offsets:
+            if done_t >= per:
+                break
+            t = time.time()
+            oracle.count_maps(adj, g, root_begin=int(off), root_stride=stride, threads=threads)
+            done_t += time.time() - t
+            done_roots += len(range(int(off), n, stride))
+            if done_roots >= n:
+                break
+        frac = done_roots / n
+        est += done_t / frac
+        parts.append(f"{name}: {done_roots} of {n} roots in {done_t:.1f} s")
+    return {"value": est, "unit": "s", "cores": threads, "kind": "oracle",
+            "sample": "; ".join(parts) + f" (uniform random strided root sets; CSR build {build_s:.1f} s excluded)",
+            "lower_bound": lower}
+
+
+# ------------------------------------------------------- multi-rank helpers
+
+def shard_range(ntasks, rank, world):
+    """Contiguous share [lo, hi) of ntasks edge tasks for one rank."""
+    return ntasks * rank // world, ntasks * (rank + 1) // world
+
+
+def allreduce_counts(counts, device=None):
+    """Exact sum over ranks of non-negative integer counts (< 2^64 each and in
+    total): each count travels as two 32-bit halves in int64 lanes."""
+    import torch
+    import torch.distributed as dist
+    halves = torch.tensor([[c >> 32, c & 0xFFFFFFFF] for c in counts], dtype=torch.int64, device=device)
+    dist.all_reduce(halves)
+    return [(int(h) << 32) + int(l) for h, l in halves.tolist()]
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in ("count.cu", "plan.h", "planner.cpp"):
+        with open(os.path.join(ROOT, "paper_2009_10955_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload):
+    """Per-launch DRAM bytes of the count kernel from a committed ncu summary,
+    used only while the kernel source is unchanged since the capture."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        e = t.get(workload)
+        if e and e.get("source_hash") == source_hash():
+            return e["dram_bytes_per_step"]
+    except Exception:
+        pass
+    return None
+
+
+def gpu_arm(a, rank, world):
+    import torch
+    import torch.distributed as dist
+    from paper_2009_10955_gb300 import native
+    N = native()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    wl = WORKLOADS[a.workload]
+    pats = a.patterns.split(",") if a.patterns else wl["patterns"]
+    n, src, dst = workload_edges(wl["graph"])
+
+    t = time.time()
+    g = N.gp_graph_create_edges(src, dst, n, N.GP_DEGREE_ORDER, stream=stream)
+    torch.cuda.synchronize()
+    build_s = time.time() - t
+    st = g.stats(stream=stream)
+    nnz = g.device_csr()[2]
+    plans, plan_s = {}, {}
+    for p in pats:
+        t = time.time()
+        plans[p] = N.gp_schedule(N.gp_pattern_create(named_pattern(p)), g, top_k=1, stream=stream)
+        plan_s[p] = time.time() - t
+    # this rank's share of every pattern's edge tasks
+    lo, hi = shard_range(nnz, rank, world)
+
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ms = ctypes.c_float()
+
+    def count(p, timed):
+        flush.fill_(1)                                     # evict the graph from L2
+        o = N.make_opts(task_begin=lo, task_end=hi, kernel_ms=ctypes.pointer(ms))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        status, c = N.gp_count(g, plans[p], 0, o, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        if status != N.GP_OK:
+            raise RuntimeError(f"count of {p} returned status {status}")
+        return c, e0.elapsed_time(e1), ms.value
+
+    # algorithmic bytes per pattern (instrumented kernel, untimed)
+    algo = {}
+    for p in pats:
+        b = ctypes.c_uint64()
+        o = N.make_opts(task_begin=lo, task_end=hi, flags=N.GP_COUNT_STATS, algo_bytes=ctypes.pointer(b))
+        N.gp_count(g, plans[p], 0, o, stream=stream)
+        algo[p] = b.value
+
+    for _ in range(a.warmup):
+        for p in pats:
+            count(p, False)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    clocks = ClockSampler(uuid if uuid.startswith("GPU-") else "GPU-" + uuid)
+    N.gp_take_launch_count()
+    step_ms, kern_ms, counts = [], {p: [] for p in pats}, {}
+    for _ in range(a.steps):
+        tot = 0.0
+        for p in pats:
+            c, call_ms, kms = count(p, True)
+            tot += call_ms
+            kern_ms[p].append(kms)
+            counts[p] = c
+        step_ms.append(tot)
+    launches = N.gp_take_launch_count()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+
+    # sum partial counts over ranks (the one exchange of the sharded path)
+    if world > 1:
+        summed = allreduce_counts([counts[p] for p in pats], device=dev)
+        counts = dict(zip(pats, summed))
+        t_local = torch.tensor([statistics.mean(step_ms)], device=dev)
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+        mean_step = float(t_local[0])
+    else:
+        mean_step = statistics.mean(step_ms)
+
+    # end to end through the C ABI with host buffers: graph from host pairs,
+    # planning, counts and 8-byte results back
+    e2e_ms = []
+    for _ in range(max(1, min(3, a.steps))):
+        torch.cuda.synchronize()
+        t = time.time()
+        g2 = N.gp_graph_create_edges(src, dst, n, N.GP_DEGREE_ORDER, stream=stream)
+        for p in pats:
+            s2 = N.gp_schedule(N.gp_pattern_create(named_pattern(p)), g2, top_k=1, stream=stream)
+            N.gp_count(g2, s2, 0, N.make_opts(task_begin=lo, task_end=hi), stream=stream)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.time() - t) * 1000.0)
+        del g2
+
+    hbm, peak_kind = peaks()
+    mean_kern = {p: statistics.mean(v) for p, v in kern_ms.items()}
+    kern_total_ms = sum(mean_kern.values())
+    algo_total = sum(algo.values())
+    achieved = algo_total / (kern_total_ms / 1000.0) / 1e9 if kern_total_ms > 0 else 0.0
+    traffic = recorded_traffic(a.workload)
+    out = {
+        "metric": "pattern-count time (s)",
+        "value": mean_step / 1000.0,
+        "unit": "s",
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": mean_step,
+        "higher_is_better": False,
+        "scaling": "strong",
+        "vs_baseline": None,
+        "dtype": "int32",
+        "data": "synthetic",
+        "config": {
+            "workload": a.workload,
+            "graph": wl["graph"],
+            "n": st["n"], "m_undirected": st["m"], "max_deg": st["max_deg"],
+            "patterns": pats,
+            "counts": {p: counts[p] for p in pats},
+            "per_pattern_s": {p: mean_kern[p] / 1000.0 for p in pats},
+            "plans": {p: plans[p].get(0)[:2] for p in pats},
+            "graph_build_s": build_s,
+            "plan_s": plan_s,
+            "l2": "flushed (512 MB write) before every count",
+            "step": "one count of each pattern, device-resident graph",
+            "parallelism": f"edge tasks sharded over {world} GPU(s)",
+        },
+        "e2e": {"value": statistics.mean(e2e_ms) / 1000.0, "unit": "s",
+                "h2d_bytes_per_step": int(src.nbytes + dst.nbytes),
+                "d2h_bytes_per_step": 8 * len(pats),
+                "includes": "graph build from host pairs, planning, counts, results to host"},
+        "gpu_launches": launches // max(1, a.steps),
+        "roofline": {
+            "bound": "hbm",
+            "achieved": achieved,
+            "peak": hbm,
+            "unit": "GB/s",
+            "frac": achieved / hbm,
+            "traffic": traffic,
+            "kernel": "k_count",
+            "algorithmic_bytes_per_step": algo_total,
+            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
+        },
+        "clocks": clk,
+    }
+    return out, (n, src, dst, pats)
+
+
+def reference_arm(a):
+    """The oracle on the host cores, each step a bounded random root sample."""
+    wl = WORKLOADS[a.workload]
+    pats = a.patterns.split(",") if a.patterns else wl["patterns"]
+    n, src, dst = workload_edges(wl["graph"])
+    per_step = max(2.0, 150.0 / max(1, a.steps + a.warmup))
+    vals = []
+    cb = None
+    for i in range(a.warmup + a.steps):
+        cb = cpu_baseline(n, src, dst, pats, per_step)
+        if i >= a.warmup:
+            vals.append(cb["value"])
+    v = statistics.mean(vals)
+    cb["value"] = v
+    return {"metric": "pattern-count time (s)", "value": v, "unit": "s", "n_gpus": 0, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": v * 1000.0, "higher_is_better": False, "impl": "reference",
+            "scaling": "strong", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": a.workload, "graph": wl["graph"], "patterns": pats},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if a.impl == "reference":
+        if rank == 0:
+            print(json.dumps(reference_arm(a)), flush=True)
+        return
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    out, (n, src, dst, pats) = gpu_arm(a, rank, world)
+    if rank == 0:
+        if world == 1 and not a.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(n, src, dst, pats, a.cpu_seconds)
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

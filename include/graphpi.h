@@ -1,0 +1,233 @@
+/* graphpi.h -- C ABI of libgraphpi_gb300.so, a GB300 (sm_103a) engine that
+ * counts the embeddings of a small connected pattern in a large undirected
+ * graph with the method of GraphPi (Shi, Zhai, Xu, Zhai, SC 2020).
+ *
+ * Problem (Section II-A): a pattern P = (V_p, E_p), 3 <= |V_p| <= 7, and a
+ * data graph G = (V, E), both undirected and unlabeled. An embedding is a
+ * distinct subgraph of G isomorphic to P under an injective map
+ * id : V_p -> V that sends every pattern edge to a graph edge (non-induced).
+ * Maps that differ by an automorphism of P are one embedding (Section II-B),
+ * so the count is #maps / |Aut(P)|.
+ *
+ * Method: the count is produced by a nested-loop search in a matching order
+ * (a "schedule", Section II-B) whose loops range over intersections of
+ * sorted neighbour lists (Section IV-B, IV-E), pruned by asymmetric
+ * restrictions id(a) > id(b) produced by 2-cycle automorphism elimination
+ * (Algorithm 1, Section IV-A), with the configuration chosen by the
+ * performance model of Section IV-C. The API takes "a pattern and a data
+ * graph in the form of adjacency lists" (Section III).
+ *
+ * Conventions for every call:
+ *  - Return value: GP_OK (0) on success, GP_PARTIAL (> 0) for a count that
+ *    stopped early and can be resumed, a negative GP_ERR_* code otherwise.
+ *    A failed call writes none of its outputs. gp_last_error() gives a
+ *    human-readable detail for the calling thread's last failure.
+ *  - Handles are opaque, created by the library and released by the
+ *    matching *_destroy call (NULL is accepted and ignored). Handles are
+ *    read-only after creation and may be shared between threads and
+ *    streams, except that a graph must not be destroyed while a count on it
+ *    is in flight.
+ *  - Streams: a `void* stream` is a cudaStream_t (NULL = the legacy default
+ *    stream). Device work runs on that stream. Every call documents whether
+ *    it synchronises the stream before returning.
+ *  - Array arguments are host pointers unless GP_DEVICE_PTRS is set, in
+ *    which case they are device pointers on the current CUDA device.
+ *  - Nothing is ever aborted: bad arguments return GP_ERR_ARG.
+ */
+#ifndef GRAPHPI_GB300_H
+#define GRAPHPI_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t gp_status;
+
+#define GP_OK            0
+#define GP_PARTIAL       1   /* count stopped at its budget; resumable            */
+#define GP_ERR_ARG      -1   /* bad argument (null pointer, size, id range)      */
+#define GP_ERR_PATTERN  -2   /* pattern not symmetric 0/1, self loop, not
+                                connected, or k outside [3, 7]                   */
+#define GP_ERR_NOMEM    -3   /* host or device allocation failed                 */
+#define GP_ERR_CUDA     -4   /* a CUDA call failed (detail in gp_last_error)     */
+#define GP_ERR_OVERFLOW -5   /* the count does not fit in 64 bits                */
+#define GP_ERR_TIMEOUT  -6   /* the device-side budget expired (see opts)       */
+#define GP_ERR_SCRATCH  -7   /* scratch memory too small for this plan/graph     */
+#define GP_ERR_INTERNAL -8   /* invariant broken inside the library              */
+
+/* gp_graph_create_* flags */
+#define GP_DEVICE_PTRS   1u  /* input arrays are device pointers                 */
+#define GP_DEGREE_ORDER  2u  /* relabel vertices by non-increasing degree
+                                (ties by id) before building the CSR; counts are
+                                label-invariant, the relabel only speeds the
+                                restricted loops                                  */
+#define GP_ASSUME_CLEAN  4u  /* gp_graph_create_csr: lists are already sorted,
+                                symmetric, loop-free and duplicate-free           */
+
+typedef struct gp_graph gp_graph;
+typedef struct gp_pattern gp_pattern;
+typedef struct gp_schedules gp_schedules;  /* ranked plans of one pattern */
+
+/* ------------------------------------------------------------------ graph */
+
+/* Build the device-resident data graph from m undirected pairs over [0, n):
+ * self loops dropped, both directions inserted, duplicates removed, every
+ * neighbour list sorted ascending, stored as CSR with int64 row offsets and
+ * int32 column ids (Section IV-E). src and dst have m entries each; n >= 0,
+ * m >= 0, n < 2^31 - 1. Ids outside [0, n) give GP_ERR_ARG (checked on the
+ * device before any output is produced). Input arrays are copied; the caller
+ * keeps ownership. Runs on `stream` and synchronises it before returning. */
+gp_status gp_graph_create_edges(const int32_t* src, const int32_t* dst, int64_t m, int32_t n,
+                                uint32_t flags, void* stream, gp_graph** out);
+
+/* Build the graph from an adjacency-list (CSR) description: row_ptr has
+ * n + 1 non-decreasing int64 entries starting at 0, col has row_ptr[n]
+ * int32 ids in [0, n). Unless GP_ASSUME_CLEAN is set the lists are cleaned
+ * exactly as gp_graph_create_edges does (each (u, col) is one pair). Input
+ * arrays are copied. Synchronises `stream`. */
+gp_status gp_graph_create_csr(const int64_t* row_ptr, const int32_t* col, int32_t n,
+                              uint32_t flags, void* stream, gp_graph** out);
+
+/* Graph statistics used by the performance model (Section IV-C): vertex
+ * count, undirected edge count |E|, maximum degree, and tri_cnt, the number
+ * of triangles counted once per ordered vertex triple (6 x the number of
+ * triangles). tri_cnt is computed on first request with the counting
+ * kernel and cached; pass NULL to skip it. Synchronises `stream` when it has
+ * to compute tri_cnt. */
+gp_status gp_graph_stats(gp_graph* g, int64_t* n, int64_t* m_undirected, int32_t* max_deg,
+                         uint64_t* tri_cnt, void* stream);
+
+/* Copy the CSR back to host buffers (row_ptr: n + 1 entries, col: 2|E|
+ * entries; either may be NULL) and, when GP_DEGREE_ORDER was used, the map
+ * new id -> input id (perm: n entries, may be NULL; identity otherwise).
+ * Synchronous. */
+gp_status gp_graph_copy_csr(const gp_graph* g, int64_t* row_ptr, int32_t* col, int32_t* perm);
+
+/* Device pointers of the CSR (valid until gp_graph_destroy). */
+gp_status gp_graph_device_csr(const gp_graph* g, const int64_t** row_ptr, const int32_t** col,
+                              int64_t* nnz);
+
+void gp_graph_destroy(gp_graph* g);
+
+/* ---------------------------------------------------------------- pattern */
+
+/* Pattern from a k x k row-major 0/1 adjacency matrix (host memory),
+ * 3 <= k <= 7, symmetric, zero diagonal, connected (else GP_ERR_PATTERN).
+ * Computes the automorphism group (Section IV-A) on creation. */
+gp_status gp_pattern_create(const uint8_t* adj, int32_t k, gp_pattern** out);
+
+/* |Aut(P)|: permutations of V_p that preserve E_p. */
+gp_status gp_pattern_aut_count(const gp_pattern* p, uint64_t* out);
+
+/* Restriction sets produced by Algorithm 1 (2-cycle based automorphism
+ * elimination), each validated on the k-vertex complete graph. *count
+ * receives how many there are (the search stops after `cap` sets, 0 = the
+ * library's default cap). With pairs != NULL, set `idx` is written as
+ * pairs[2r], pairs[2r+1] = (a, b) meaning id(a) > id(b), r < *n_pairs <= 21. */
+gp_status gp_pattern_restriction_sets(gp_pattern* p, int32_t cap, int32_t* count,
+                                      int32_t idx, int32_t* pairs, int32_t* n_pairs);
+
+/* Efficient schedules of Section IV-B (phase 1: every prefix connected;
+ * phase 2: the last k' searched vertices pairwise non-adjacent, with k' the
+ * largest value <= the maximum independent set size that keeps at least
+ * one schedule). *count receives their number, *kprime the k' used; with
+ * order != NULL schedule `idx` is written (k entries, pattern vertex ids in
+ * search order). */
+gp_status gp_pattern_schedules(const gp_pattern* p, int32_t* count, int32_t* kprime,
+                               int32_t idx, int32_t* order);
+
+void gp_pattern_destroy(gp_pattern* p);
+
+/* ------------------------------------------------------------- schedules */
+
+/* Rank every configuration (efficient schedule x restriction set) with the
+ * performance model cost_i = l_i (1 - f_i) (c_i + cost_{i+1}),
+ * cost_n = l_n (1 - f_n) (Section IV-C), using the graph's statistics
+ * (g == NULL: |V| = 2^20, |E| = 8 |V|, tri_cnt = 6 |E|), and keep the top_k
+ * (>= 1) cheapest as ready-to-run plans. May synchronise `stream` (tri_cnt). */
+gp_status gp_schedule(const gp_pattern* p, gp_graph* g, int32_t top_k, void* stream,
+                      gp_schedules** out);
+
+/* A single explicit configuration: `order` (k pattern vertices in search
+ * order; every prefix must be connected) and n_restr restrictions
+ * restr[2r] > restr[2r+1]. The set must be valid (Algorithm 1, validate),
+ * else GP_ERR_PATTERN. */
+gp_status gp_schedule_explicit(const gp_pattern* p, const int32_t* order, const int32_t* restr,
+                               int32_t n_restr, gp_schedules** out);
+
+/* Number of plans held. */
+gp_status gp_schedule_size(const gp_schedules* s, int32_t* count);
+
+/* Plan idx: order[k], restrictions (restr[2r] > restr[2r+1], up to 21 pairs;
+ * may be NULL), their number and the predicted cost (may be NULL). */
+gp_status gp_schedule_get(const gp_schedules* s, int32_t idx, int32_t* order, int32_t* restr,
+                          int32_t* n_restr, double* predicted_cost);
+
+/* Performance-model cost of one configuration for given |V|, |E|
+ * (undirected) and tri_cnt (ordered). */
+gp_status gp_config_cost(const gp_pattern* p, const int32_t* order, const int32_t* restr,
+                         int32_t n_restr, double n_vertices, double n_edges, double tri_cnt,
+                         double* cost);
+
+void gp_schedule_destroy(gp_schedules* s);
+
+/* ----------------------------------------------------------------- count */
+
+/* Optional tuning and control for gp_count / gp_count_batch. Zero fields
+ * take the library defaults. */
+typedef struct gp_count_opts {
+    int32_t struct_size;      /* sizeof(gp_count_opts)                               */
+    int32_t warps_per_block;  /* 1..32                                               */
+    int32_t blocks_per_sm;    /* resident blocks per SM for the persistent grid       */
+    int32_t chunk;            /* edge tasks claimed per work-queue grab               */
+    int32_t split;            /* second-level split: an edge task whose level-2
+                                 candidate list is longer than this is cut into
+                                 pieces of this many candidates (0 = default)        */
+    int32_t flags;            /* GP_COUNT_STATS                                      */
+    int64_t task_begin;       /* first edge task (CSR entry) to process              */
+    int64_t task_end;         /* one past the last (0 = all)                         */
+    int64_t budget_cycles;    /* per-warp clock64 budget; 0 = unlimited              */
+    int64_t* resume_cursor;   /* host out: with GP_PARTIAL, where to resume          */
+    float* kernel_ms;         /* host out (may be NULL): device time of the counting
+                                 kernel, from CUDA events recorded around its launch
+                                 on the caller's stream                               */
+    uint64_t* algo_bytes;     /* host out (with GP_COUNT_STATS): algorithmic bytes of
+                                 the count -- 4 bytes per element of every clipped
+                                 intersection operand, per stored intersection
+                                 result and per iterated candidate                   */
+} gp_count_opts;
+
+/* gp_count_opts.flags */
+#define GP_COUNT_STATS 1   /* run the instrumented kernel that tallies algo_bytes
+                              (slower; for measurement only)                      */
+
+/* Count the embeddings of the pattern of `s` in `g` with plan `idx`.
+ * Every embedding is counted exactly once (restrictions, Algorithm 1).
+ * Writes *out (host) on GP_OK. GP_ERR_OVERFLOW when the count needs more
+ * than 64 bits. Runs on `stream` and synchronises it before returning; the
+ * only device-to-host traffic is the 16-byte result and an error word. */
+gp_status gp_count(gp_graph* g, const gp_schedules* s, int32_t idx, const gp_count_opts* opts,
+                   void* stream, uint64_t* out);
+
+/* Count several (graph, schedule, plan) jobs in ONE persistent launch; work
+ * items of all jobs share one device work queue. out[j] receives job j's
+ * count. All graphs must live on the current device. Synchronises. */
+gp_status gp_count_batch(gp_graph* const* graphs, const gp_schedules* const* scheds,
+                         const int32_t* idx, int32_t njobs, const gp_count_opts* opts,
+                         void* stream, uint64_t* out);
+
+/* ------------------------------------------------------------------ misc */
+
+const char* gp_status_str(gp_status s);
+const char* gp_last_error(void);
+/* Number of kernel launches the library issued on this thread since the
+ * last call of this function (a launch counter for benchmarking). */
+int64_t gp_take_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRAPHPI_GB300_H */

@@ -52,7 +52,7 @@ def _load():
         lib.oracle_aut_count.argtypes = [i32, P, P]
         lib.oracle_count_maps.argtypes = [i32, P, i32, P, P, i32, i32, i32, i32, P, P]
         lib.oracle_count.argtypes = [i32, P, i32, P, P, i32, P]
-        lib.oracle_count_restricted.argtypes = [i32, P, P, i32, P, i32, P, P, i32, P, P]
+        lib.oracle_count_restricted.argtypes = [i32, P, P, i32, P, i32, P, P, i32, i32, i32, P, P]
         lib.oracle_triangles.argtypes = [i32, P, P, i32, P]
         for f in (lib.oracle_build_csr, lib.oracle_aut_count, lib.oracle_count_maps,
                   lib.oracle_count, lib.oracle_count_restricted, lib.oracle_triangles):
@@ -134,9 +134,10 @@ def count(adj, g, threads=None):
     return maps // aut
 
 
-def count_restricted(adj, order, restrictions, g, threads=None):
+def count_restricted(adj, order, restrictions, g, threads=None, root_begin=0, root_end=None):
     """Maps found in matching order ``order`` that obey every restriction
-    ``(a, b)``: id(a) > id(b)."""
+    ``(a, b)``: id(a) > id(b), with the first searched vertex's image in
+    ``[root_begin, root_end)``."""
     adj = _adj(adj)
     k = adj.shape[0]
     order = np.ascontiguousarray(order, dtype=np.int32)
@@ -149,11 +150,23 @@ def count_restricted(adj, order, restrictions, g, threads=None):
     hi = np.zeros(1, dtype=np.uint64)
     lo = np.zeros(1, dtype=np.uint64)
     rc = _load().oracle_count_restricted(k, _p(adj), _p(order), nres, _p(res), g.n,
-                                         _p(g.row_ptr), _p(g.col), threads or default_threads(),
-                                         _p(hi), _p(lo))
+                                         _p(g.row_ptr), _p(g.col), root_begin,
+                                         g.n if root_end is None else root_end,
+                                         threads or default_threads(), _p(hi), _p(lo))
     if rc:
         raise ValueError(f"oracle_count_restricted failed ({rc})")
     return (int(hi[0]) << 64) | int(lo[0])
+
+
+def degree_relabel(g):
+    """Relabel vertices by non-increasing degree, ties by smaller id (the
+    definition of the library's degree order). Returns (graph, new2old)."""
+    deg = np.diff(g.row_ptr)
+    new2old = np.lexsort((np.arange(g.n), -deg)).astype(np.int32)
+    old2new = np.empty(g.n, dtype=np.int32)
+    old2new[new2old] = np.arange(g.n, dtype=np.int32)
+    src = np.repeat(np.arange(g.n, dtype=np.int32), deg)
+    return build_csr(g.n, old2new[src], old2new[g.col]), new2old
 
 
 def triangles(g, threads=None):

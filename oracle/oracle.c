@@ -269,13 +269,17 @@ int oracle_count(int32_t k, const uint8_t* adj,
 int oracle_count_restricted(int32_t k, const uint8_t* adj, const int32_t* order,
                             int32_t nres, const int32_t* res,
                             int32_t n, const int64_t* row_ptr, const int32_t* col,
+                            int32_t root_begin, int32_t root_end,
                             int32_t nthreads, uint64_t* hi, uint64_t* lo) {
     if (!hi || !lo || !order || (nres > 0 && !res) || nres < 0) return -1;
     walk_t* w = (walk_t*)malloc(sizeof(walk_t));
     if (!w) return -2;
     int rc = setup_walk(w, k, adj, order, nres, res, n, row_ptr, col);
     if (rc) { free(w); return rc; }
-    w->root_begin = 0; w->root_end = n; w->root_stride = 1;
+    if (root_begin < 0) root_begin = 0;
+    if (root_end > n) root_end = n;
+    if (root_end < root_begin) root_end = root_begin;
+    w->root_begin = root_begin; w->root_end = root_end; w->root_stride = 1;
     u128 total = 0;
     rc = run_walk(w, nthreads, &total);
     free(w);

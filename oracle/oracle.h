@@ -56,12 +56,15 @@ int oracle_count(int32_t k, const uint8_t* adj,
                  int32_t nthreads, uint64_t* out);
 
 /* Maps enumerated in the given matching order (Section II-B) that also obey
- * every restriction id(res[2i]) > id(res[2i+1]) (Section II-B). Vertices are
- * pattern vertex numbers; order is a permutation of 0..k-1. With a correct
- * restriction set this equals count(P, G) (Algorithm 1, validate). */
+ * every restriction id(res[2i]) > id(res[2i+1]) (Section II-B), with the
+ * image of the first searched vertex in [root_begin, root_end). Vertices are
+ * pattern vertex numbers; order is a permutation of 0..k-1 whose prefixes
+ * are connected. With a correct restriction set and all roots this equals
+ * count(P, G) (Algorithm 1, validate). */
 int oracle_count_restricted(int32_t k, const uint8_t* adj, const int32_t* order,
                             int32_t nres, const int32_t* res,
                             int32_t n, const int64_t* row_ptr, const int32_t* col,
+                            int32_t root_begin, int32_t root_end,
                             int32_t nthreads, uint64_t* hi, uint64_t* lo);
 
 /* Unordered triangles {a, b, c} of the graph (the cost model's tri_cnt,

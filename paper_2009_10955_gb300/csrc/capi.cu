@@ -1,0 +1,514 @@
+// capi.cu -- the C ABI of libgraphpi_gb300.so (declared in include/graphpi.h).
+// Argument checking, handle management and host<->device marshalling; all
+// graph and counting work runs in the kernels of graph.cu and count.cu.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <vector>
+
+#include "engine.h"
+#include "planner.h"
+
+struct gp_pattern {
+    gp::PatternInfo info;
+};
+
+struct gp_schedules {
+    int k = 0;
+    std::vector<gp::Config> configs;
+    std::vector<GpPlan> plans;
+};
+
+namespace gp {
+
+namespace {
+thread_local char t_error[512] = "";
+thread_local int64_t t_launches = 0;
+}  // namespace
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(t_error, sizeof(t_error), fmt, ap);
+    va_end(ap);
+}
+
+void count_launch(int n) { t_launches += n; }
+
+namespace {
+
+gp_status fail(gp_status s, const char* msg) {
+    set_error("%s", msg);
+    return s;
+}
+
+// Stream-ordered device buffer released on scope exit.
+struct DevBuf {
+    void* p = nullptr;
+    cudaStream_t st;
+    explicit DevBuf(cudaStream_t s) : st(s) {}
+    ~DevBuf() { if (p) cudaFreeAsync(p, st); }
+};
+
+void free_graph(gp_graph* g) {
+    if (!g) return;
+    if (g->row_ptr) cudaFree(g->row_ptr);
+    if (g->col) cudaFree(g->col);
+    if (g->perm) cudaFree(g->perm);
+    delete g;
+}
+
+gp_status ensure_device(const gp_graph* g) {
+    int cur = 0;
+    GP_CUDA_TRY(cudaGetDevice(&cur));
+    if (cur != g->device) GP_CUDA_TRY(cudaSetDevice(g->device));
+    return GP_OK;
+}
+
+// Triangle plan: schedule (0, 1, 2) with id(0) > id(1) > id(2).
+gp_status triangle_count(gp_graph* g, cudaStream_t st, uint64_t* out) {
+    static const uint8_t tri[9] = {0, 1, 1, 1, 0, 1, 1, 1, 0};
+    PatternInfo info;
+    std::string err;
+    if (!pattern_init(info, tri, 3, err)) return fail(GP_ERR_INTERNAL, err.c_str());
+    const int8_t sched[3] = {0, 1, 2};
+    ResMask res = (1ull << res_bit(0, 1)) | (1ull << res_bit(1, 2));
+    CountJob job;
+    std::memset(&job, 0, sizeof(job));
+    if (!compile_plan(info, sched, res, &job.plan, err)) return fail(GP_ERR_INTERNAL, err.c_str());
+    job.row_ptr = g->row_ptr;
+    job.col = g->col;
+    job.n = g->n;
+    job.slot_cap = g->max_deg > 0 ? g->max_deg : 1;
+    job.task_begin = 0;
+    job.ntasks = g->nnz;
+    job.task_offset = 0;
+    uint64_t res2[2] = {0, 0};
+    int64_t done = 0;
+    gp_status rc = run_count(&job, 1, LaunchOpts(), st, res2, &done);
+    if (rc != GP_OK) return rc;
+    if (res2[1]) return fail(GP_ERR_OVERFLOW, "triangle count overflows 64 bits");
+    *out = res2[0];
+    return GP_OK;
+}
+
+gp_status make_job(gp_graph* g, const gp_schedules* s, int32_t idx, const gp_count_opts* opts,
+                   CountJob* job) {
+    if (!g || !s) return fail(GP_ERR_ARG, "null graph or schedule");
+    if (idx < 0 || idx >= (int32_t)s->plans.size()) return fail(GP_ERR_ARG, "plan index out of range");
+    std::memset(job, 0, sizeof(*job));
+    job->plan = s->plans[idx];
+    job->row_ptr = g->row_ptr;
+    job->col = g->col;
+    job->n = g->n;
+    job->slot_cap = g->max_deg > 0 ? g->max_deg : 1;
+    int64_t b = 0, e = g->nnz;
+    if (opts) {
+        if (opts->task_begin < 0 || opts->task_end < 0) return fail(GP_ERR_ARG, "negative task range");
+        b = std::min<int64_t>(opts->task_begin, g->nnz);
+        if (opts->task_end > 0) e = std::min<int64_t>(opts->task_end, g->nnz);
+        if (e < b) e = b;
+    }
+    job->task_begin = b;
+    job->ntasks = e - b;
+    return GP_OK;
+}
+
+LaunchOpts launch_opts(const gp_count_opts* o) {
+    LaunchOpts lo;
+    if (o) {
+        if (o->blocks_per_sm > 0) lo.blocks_per_sm = o->blocks_per_sm;
+        if (o->chunk > 0) lo.chunk = o->chunk;
+        if (o->budget_cycles > 0) lo.budget_cycles = o->budget_cycles;
+        lo.stats = (o->flags & GP_COUNT_STATS) != 0;
+    }
+    return lo;
+}
+
+bool opts_ok(const gp_count_opts* o) {
+    return !o || (o->struct_size == (int32_t)sizeof(gp_count_opts));
+}
+
+}  // namespace
+}  // namespace gp
+
+using namespace gp;
+
+extern "C" {
+
+const char* gp_status_str(gp_status s) {
+    switch (s) {
+        case GP_OK: return "GP_OK";
+        case GP_PARTIAL: return "GP_PARTIAL";
+        case GP_ERR_ARG: return "GP_ERR_ARG";
+        case GP_ERR_PATTERN: return "GP_ERR_PATTERN";
+        case GP_ERR_NOMEM: return "GP_ERR_NOMEM";
+        case GP_ERR_CUDA: return "GP_ERR_CUDA";
+        case GP_ERR_OVERFLOW: return "GP_ERR_OVERFLOW";
+        case GP_ERR_TIMEOUT: return "GP_ERR_TIMEOUT";
+        case GP_ERR_SCRATCH: return "GP_ERR_SCRATCH";
+        case GP_ERR_INTERNAL: return "GP_ERR_INTERNAL";
+        default: return "GP_UNKNOWN";
+    }
+}
+
+const char* gp_last_error(void) { return t_error; }
+
+int64_t gp_take_launch_count(void) {
+    int64_t n = t_launches;
+    t_launches = 0;
+    return n;
+}
+
+gp_status gp_graph_create_edges(const int32_t* src, const int32_t* dst, int64_t m, int32_t n,
+                                uint32_t flags, void* stream, gp_graph** out) {
+    if (!out) return fail(GP_ERR_ARG, "out is null");
+    if (n < 0 || n >= INT32_MAX || m < 0) return fail(GP_ERR_ARG, "bad n or m");
+    if (m > 0 && (!src || !dst)) return fail(GP_ERR_ARG, "null edge arrays");
+    if (flags & ~(GP_DEVICE_PTRS | GP_DEGREE_ORDER)) return fail(GP_ERR_ARG, "unknown flag");
+    if (m > ((int64_t)1 << 40)) return fail(GP_ERR_ARG, "too many pairs");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::unique_ptr<gp_graph, void (*)(gp_graph*)> g(new (std::nothrow) gp_graph(), free_graph);
+    if (!g) return fail(GP_ERR_NOMEM, "host allocation failed");
+    GP_CUDA_TRY(cudaGetDevice(&g->device));
+    const int32_t* ds = src;
+    const int32_t* dd = dst;
+    DevBuf bs(st), bd(st);
+    if (!(flags & GP_DEVICE_PTRS) && m > 0) {
+        GP_CUDA_TRY(cudaMallocAsync(&bs.p, sizeof(int32_t) * (size_t)m, st));
+        GP_CUDA_TRY(cudaMallocAsync(&bd.p, sizeof(int32_t) * (size_t)m, st));
+        GP_CUDA_TRY(cudaMemcpyAsync(bs.p, src, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, st));
+        GP_CUDA_TRY(cudaMemcpyAsync(bd.p, dst, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, st));
+        ds = static_cast<const int32_t*>(bs.p);
+        dd = static_cast<const int32_t*>(bd.p);
+    }
+    gp_status rc = build_graph(ds, dd, m, n, (flags & GP_DEGREE_ORDER) != 0, st, g.get());
+    if (rc != GP_OK) return rc;
+    *out = g.release();
+    return GP_OK;
+}
+
+gp_status gp_graph_create_csr(const int64_t* row_ptr, const int32_t* col, int32_t n,
+                              uint32_t flags, void* stream, gp_graph** out) {
+    if (!out || !row_ptr) return fail(GP_ERR_ARG, "null argument");
+    if (n < 0 || n >= INT32_MAX) return fail(GP_ERR_ARG, "bad n");
+    if (flags & ~(GP_DEVICE_PTRS | GP_DEGREE_ORDER | GP_ASSUME_CLEAN)) return fail(GP_ERR_ARG, "unknown flag");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool dev = (flags & GP_DEVICE_PTRS) != 0;
+    int64_t nnz = 0;
+    std::vector<int64_t> h_rp;
+    if (dev) {
+        GP_CUDA_TRY(cudaMemcpyAsync(&nnz, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        GP_CUDA_TRY(cudaStreamSynchronize(st));
+    } else {
+        if (row_ptr[0] != 0) return fail(GP_ERR_ARG, "row_ptr[0] must be 0");
+        for (int32_t u = 0; u < n; ++u)
+            if (row_ptr[u + 1] < row_ptr[u]) return fail(GP_ERR_ARG, "row_ptr must be non-decreasing");
+        nnz = row_ptr[n];
+    }
+    if (nnz < 0) return fail(GP_ERR_ARG, "negative entry count");
+    if (nnz > 0 && !col) return fail(GP_ERR_ARG, "null col");
+    std::unique_ptr<gp_graph, void (*)(gp_graph*)> g(new (std::nothrow) gp_graph(), free_graph);
+    if (!g) return fail(GP_ERR_NOMEM, "host allocation failed");
+    GP_CUDA_TRY(cudaGetDevice(&g->device));
+    DevBuf brp(st), bcol(st);
+    const int64_t* drp = row_ptr;
+    const int32_t* dcol = col;
+    if (!dev) {
+        GP_CUDA_TRY(cudaMallocAsync(&brp.p, sizeof(int64_t) * ((size_t)n + 1), st));
+        GP_CUDA_TRY(cudaMallocAsync(&bcol.p, sizeof(int32_t) * (size_t)(nnz ? nnz : 1), st));
+        GP_CUDA_TRY(cudaMemcpyAsync(brp.p, row_ptr, sizeof(int64_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, st));
+        if (nnz) GP_CUDA_TRY(cudaMemcpyAsync(bcol.p, col, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, st));
+        drp = static_cast<const int64_t*>(brp.p);
+        dcol = static_cast<const int32_t*>(bcol.p);
+    }
+    if ((flags & GP_ASSUME_CLEAN) && !(flags & GP_DEGREE_ORDER)) {
+        GP_CUDA_TRY(cudaMalloc(&g->row_ptr, sizeof(int64_t) * ((size_t)n + 1)));
+        GP_CUDA_TRY(cudaMalloc(&g->col, sizeof(int32_t) * (size_t)(nnz ? nnz : 1)));
+        GP_CUDA_TRY(cudaMemcpyAsync(g->row_ptr, drp, sizeof(int64_t) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, st));
+        if (nnz) GP_CUDA_TRY(cudaMemcpyAsync(g->col, dcol, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToDevice, st));
+        g->n = n;
+        g->nnz = nnz;
+        gp_status rc = max_degree(g->row_ptr, n, st, &g->max_deg);
+        if (rc != GP_OK) return rc;
+        *out = g.release();
+        return GP_OK;
+    }
+    DevBuf ps(st), pd(st);
+    GP_CUDA_TRY(cudaMallocAsync(&ps.p, sizeof(int32_t) * (size_t)(nnz ? nnz : 1), st));
+    GP_CUDA_TRY(cudaMallocAsync(&pd.p, sizeof(int32_t) * (size_t)(nnz ? nnz : 1), st));
+    gp_status rc = csr_to_pairs(drp, dcol, n, nnz, static_cast<int32_t*>(ps.p), static_cast<int32_t*>(pd.p), st);
+    if (rc != GP_OK) return rc;
+    rc = build_graph(static_cast<int32_t*>(ps.p), static_cast<int32_t*>(pd.p), nnz, n,
+                     (flags & GP_DEGREE_ORDER) != 0, st, g.get());
+    if (rc != GP_OK) return rc;
+    *out = g.release();
+    return GP_OK;
+}
+
+gp_status gp_graph_stats(gp_graph* g, int64_t* n, int64_t* m_undirected, int32_t* max_deg,
+                         uint64_t* tri_cnt, void* stream) {
+    if (!g) return fail(GP_ERR_ARG, "null graph");
+    if (tri_cnt) {
+        std::lock_guard<std::mutex> lock(g->mu);
+        if (!g->tri_done) {
+            gp_status rc = ensure_device(g);
+            if (rc != GP_OK) return rc;
+            uint64_t t = 0;
+            rc = triangle_count(g, static_cast<cudaStream_t>(stream), &t);
+            if (rc != GP_OK) return rc;
+            if (t > UINT64_MAX / 6) return fail(GP_ERR_OVERFLOW, "6 x triangles overflows 64 bits");
+            g->tri_cnt = 6 * t;
+            g->tri_done = true;
+        }
+        *tri_cnt = g->tri_cnt;
+    }
+    if (n) *n = g->n;
+    if (m_undirected) *m_undirected = g->nnz / 2;
+    if (max_deg) *max_deg = g->max_deg;
+    return GP_OK;
+}
+
+gp_status gp_graph_copy_csr(const gp_graph* g, int64_t* row_ptr, int32_t* col, int32_t* perm) {
+    if (!g) return fail(GP_ERR_ARG, "null graph");
+    if (row_ptr) GP_CUDA_TRY(cudaMemcpy(row_ptr, g->row_ptr, sizeof(int64_t) * ((size_t)g->n + 1), cudaMemcpyDeviceToHost));
+    if (col && g->nnz) GP_CUDA_TRY(cudaMemcpy(col, g->col, sizeof(int32_t) * (size_t)g->nnz, cudaMemcpyDeviceToHost));
+    if (perm) {
+        if (g->perm) GP_CUDA_TRY(cudaMemcpy(perm, g->perm, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToHost));
+        else for (int32_t u = 0; u < g->n; ++u) perm[u] = u;
+    }
+    return GP_OK;
+}
+
+gp_status gp_graph_device_csr(const gp_graph* g, const int64_t** row_ptr, const int32_t** col,
+                              int64_t* nnz) {
+    if (!g) return fail(GP_ERR_ARG, "null graph");
+    if (row_ptr) *row_ptr = g->row_ptr;
+    if (col) *col = g->col;
+    if (nnz) *nnz = g->nnz;
+    return GP_OK;
+}
+
+void gp_graph_destroy(gp_graph* g) { free_graph(g); }
+
+gp_status gp_pattern_create(const uint8_t* adj, int32_t k, gp_pattern** out) {
+    if (!adj || !out) return fail(GP_ERR_ARG, "null argument");
+    std::unique_ptr<gp_pattern> p(new (std::nothrow) gp_pattern());
+    if (!p) return fail(GP_ERR_NOMEM, "host allocation failed");
+    std::string err;
+    if (!pattern_init(p->info, adj, k, err)) return fail(GP_ERR_PATTERN, err.c_str());
+    *out = p.release();
+    return GP_OK;
+}
+
+gp_status gp_pattern_aut_count(const gp_pattern* p, uint64_t* out) {
+    if (!p || !out) return fail(GP_ERR_ARG, "null argument");
+    *out = p->info.auts.size();
+    return GP_OK;
+}
+
+gp_status gp_pattern_restriction_sets(gp_pattern* p, int32_t cap, int32_t* count,
+                                      int32_t idx, int32_t* pairs, int32_t* n_pairs) {
+    if (!p || !count) return fail(GP_ERR_ARG, "null argument");
+    const std::vector<ResMask>& sets = restriction_sets(p->info, cap);
+    if (pairs || n_pairs) {
+        if (idx < 0 || idx >= (int32_t)sets.size()) return fail(GP_ERR_ARG, "set index out of range");
+        int r = 0;
+        for (int a = 0; a < p->info.k; ++a)
+            for (int b = 0; b < p->info.k; ++b)
+                if (sets[idx] >> res_bit(a, b) & 1) {
+                    if (pairs) { pairs[2 * r] = a; pairs[2 * r + 1] = b; }
+                    ++r;
+                }
+        if (n_pairs) *n_pairs = r;
+    }
+    *count = (int32_t)sets.size();
+    return GP_OK;
+}
+
+gp_status gp_pattern_schedules(const gp_pattern* p, int32_t* count, int32_t* kprime,
+                               int32_t idx, int32_t* order) {
+    if (!p || !count) return fail(GP_ERR_ARG, "null argument");
+    int kp = 0;
+    const std::vector<Perm>& sc = efficient_schedules(const_cast<gp_pattern*>(p)->info, &kp);
+    if (order) {
+        if (idx < 0 || idx >= (int32_t)sc.size()) return fail(GP_ERR_ARG, "schedule index out of range");
+        for (int i = 0; i < p->info.k; ++i) order[i] = sc[idx][i];
+    }
+    *count = (int32_t)sc.size();
+    if (kprime) *kprime = kp;
+    return GP_OK;
+}
+
+void gp_pattern_destroy(gp_pattern* p) { delete p; }
+
+gp_status gp_schedule(const gp_pattern* p, gp_graph* g, int32_t top_k, void* stream, gp_schedules** out) {
+    if (!p || !out || top_k < 1) return fail(GP_ERR_ARG, "bad argument");
+    double V = (double)(1 << 20), E = 8.0 * V, T = 6.0 * E;
+    if (g) {
+        uint64_t tri = 0;
+        gp_status rc = gp_graph_stats(g, nullptr, nullptr, nullptr, &tri, stream);
+        if (rc != GP_OK) return rc;
+        V = g->n > 0 ? (double)g->n : 1.0;
+        E = g->nnz > 0 ? (double)(g->nnz / 2) : 1.0;
+        T = tri > 0 ? (double)tri : 1.0;       // keep p2 > 0 on triangle-free graphs
+    }
+    std::unique_ptr<gp_schedules> s(new (std::nothrow) gp_schedules());
+    if (!s) return fail(GP_ERR_NOMEM, "host allocation failed");
+    gp_pattern* pm = const_cast<gp_pattern*>(p);
+    s->k = p->info.k;
+    s->configs = rank_configs(pm->info, V, E, T, top_k);
+    if (s->configs.empty()) return fail(GP_ERR_PATTERN, "no configuration for this pattern");
+    for (const Config& c : s->configs) {
+        GpPlan plan;
+        std::string err;
+        if (!compile_plan(p->info, c.sched.data(), c.res, &plan, err)) return fail(GP_ERR_INTERNAL, err.c_str());
+        s->plans.push_back(plan);
+    }
+    *out = s.release();
+    return GP_OK;
+}
+
+gp_status gp_schedule_explicit(const gp_pattern* p, const int32_t* order, const int32_t* restr,
+                               int32_t n_restr, gp_schedules** out) {
+    if (!p || !order || !out || n_restr < 0 || (n_restr > 0 && !restr)) return fail(GP_ERR_ARG, "bad argument");
+    const int k = p->info.k;
+    Perm sched{};
+    for (int i = 0; i < k; ++i) {
+        if (order[i] < 0 || order[i] >= k) return fail(GP_ERR_ARG, "order entry outside the pattern");
+        sched[i] = (int8_t)order[i];
+    }
+    ResMask res = 0;
+    for (int r = 0; r < n_restr; ++r) {
+        int a = restr[2 * r], b = restr[2 * r + 1];
+        if (a < 0 || a >= k || b < 0 || b >= k || a == b) return fail(GP_ERR_ARG, "bad restriction");
+        res |= 1ull << res_bit(a, b);
+    }
+    if (!validate_set(p->info, res)) return fail(GP_ERR_PATTERN, "restriction set fails validate");
+    GpPlan plan;
+    std::string err;
+    if (!compile_plan(p->info, sched.data(), res, &plan, err)) return fail(GP_ERR_PATTERN, err.c_str());
+    std::unique_ptr<gp_schedules> s(new (std::nothrow) gp_schedules());
+    if (!s) return fail(GP_ERR_NOMEM, "host allocation failed");
+    s->k = k;
+    s->configs.push_back({0.0, sched, res});
+    s->plans.push_back(plan);
+    *out = s.release();
+    return GP_OK;
+}
+
+gp_status gp_schedule_size(const gp_schedules* s, int32_t* count) {
+    if (!s || !count) return fail(GP_ERR_ARG, "null argument");
+    *count = (int32_t)s->plans.size();
+    return GP_OK;
+}
+
+gp_status gp_schedule_get(const gp_schedules* s, int32_t idx, int32_t* order, int32_t* restr,
+                          int32_t* n_restr, double* predicted_cost) {
+    if (!s) return fail(GP_ERR_ARG, "null schedule");
+    if (idx < 0 || idx >= (int32_t)s->configs.size()) return fail(GP_ERR_ARG, "plan index out of range");
+    const Config& c = s->configs[idx];
+    if (order) for (int i = 0; i < s->k; ++i) order[i] = c.sched[i];
+    int r = 0;
+    for (int a = 0; a < s->k; ++a)
+        for (int b = 0; b < s->k; ++b)
+            if (c.res >> res_bit(a, b) & 1) {
+                if (restr) { restr[2 * r] = a; restr[2 * r + 1] = b; }
+                ++r;
+            }
+    if (n_restr) *n_restr = r;
+    if (predicted_cost) *predicted_cost = c.cost;
+    return GP_OK;
+}
+
+gp_status gp_config_cost(const gp_pattern* p, const int32_t* order, const int32_t* restr,
+                         int32_t n_restr, double n_vertices, double n_edges, double tri_cnt,
+                         double* cost) {
+    if (!p || !order || !cost || n_restr < 0 || (n_restr > 0 && !restr)) return fail(GP_ERR_ARG, "bad argument");
+    if (!(n_vertices > 0) || !(n_edges > 0) || !(tri_cnt >= 0)) return fail(GP_ERR_ARG, "bad graph statistics");
+    const int k = p->info.k;
+    int8_t sched[GP_MAX_K];
+    for (int i = 0; i < k; ++i) {
+        if (order[i] < 0 || order[i] >= k) return fail(GP_ERR_ARG, "order entry outside the pattern");
+        sched[i] = (int8_t)order[i];
+    }
+    ResMask res = 0;
+    for (int r = 0; r < n_restr; ++r) {
+        int a = restr[2 * r], b = restr[2 * r + 1];
+        if (a < 0 || a >= k || b < 0 || b >= k || a == b) return fail(GP_ERR_ARG, "bad restriction");
+        res |= 1ull << res_bit(a, b);
+    }
+    *cost = config_cost(p->info, sched, res, n_vertices, n_edges, tri_cnt);
+    return GP_OK;
+}
+
+void gp_schedule_destroy(gp_schedules* s) { delete s; }
+
+gp_status gp_count(gp_graph* g, const gp_schedules* s, int32_t idx, const gp_count_opts* opts,
+                   void* stream, uint64_t* out) {
+    if (!out) return fail(GP_ERR_ARG, "out is null");
+    if (!opts_ok(opts)) return fail(GP_ERR_ARG, "gp_count_opts.struct_size mismatch");
+    CountJob job;
+    gp_status rc = make_job(g, s, idx, opts, &job);
+    if (rc != GP_OK) return rc;
+    rc = ensure_device(g);
+    if (rc != GP_OK) return rc;
+    uint64_t res[2] = {0, 0};
+    int64_t done = 0;
+    float ms = 0.f;
+    uint64_t bytes = 0;
+    const bool want_ms = opts && opts->kernel_ms;
+    rc = run_count(&job, 1, launch_opts(opts), static_cast<cudaStream_t>(stream), res, &done,
+                   want_ms ? &ms : nullptr, &bytes);
+    if (rc != GP_OK) return rc;
+    if (res[1]) return fail(GP_ERR_OVERFLOW, "count does not fit in 64 bits");
+    if (want_ms) *opts->kernel_ms = ms;
+    if (opts && opts->algo_bytes && (opts->flags & GP_COUNT_STATS)) *opts->algo_bytes = bytes;
+    if (done < job.ntasks) {
+        if (opts && opts->resume_cursor) *opts->resume_cursor = job.task_begin + done;
+        *out = res[0];
+        return GP_PARTIAL;
+    }
+    if (opts && opts->resume_cursor) *opts->resume_cursor = job.task_begin + job.ntasks;
+    *out = res[0];
+    return GP_OK;
+}
+
+gp_status gp_count_batch(gp_graph* const* graphs, const gp_schedules* const* scheds,
+                         const int32_t* idx, int32_t njobs, const gp_count_opts* opts,
+                         void* stream, uint64_t* out) {
+    if (!graphs || !scheds || !out || njobs < 1) return fail(GP_ERR_ARG, "bad argument");
+    if (!opts_ok(opts)) return fail(GP_ERR_ARG, "gp_count_opts.struct_size mismatch");
+    if (opts && (opts->task_begin || opts->task_end)) return fail(GP_ERR_ARG, "task ranges are per gp_count only");
+    std::vector<CountJob> jobs((size_t)njobs);
+    int64_t off = 0;
+    for (int32_t j = 0; j < njobs; ++j) {
+        gp_status rc = make_job(graphs[j], scheds[j], idx ? idx[j] : 0, nullptr, &jobs[j]);
+        if (rc != GP_OK) return rc;
+        if (graphs[j]->device != graphs[0]->device) return fail(GP_ERR_ARG, "graphs on different devices");
+        jobs[j].task_offset = off;
+        off += jobs[j].ntasks;
+    }
+    gp_status rc = ensure_device(graphs[0]);
+    if (rc != GP_OK) return rc;
+    std::vector<uint64_t> res(2 * (size_t)njobs, 0);
+    int64_t done = 0;
+    LaunchOpts lo = launch_opts(opts);
+    lo.budget_cycles = 0;
+    float ms = 0.f;
+    uint64_t bytes = 0;
+    const bool want_ms = opts && opts->kernel_ms;
+    rc = run_count(jobs.data(), njobs, lo, static_cast<cudaStream_t>(stream), res.data(), &done,
+                   want_ms ? &ms : nullptr, &bytes);
+    if (rc != GP_OK) return rc;
+    if (want_ms) *opts->kernel_ms = ms;
+    if (opts && opts->algo_bytes && (opts->flags & GP_COUNT_STATS)) *opts->algo_bytes = bytes;
+    for (int32_t j = 0; j < njobs; ++j)
+        if (res[2 * j + 1]) return fail(GP_ERR_OVERFLOW, "a count does not fit in 64 bits");
+    for (int32_t j = 0; j < njobs; ++j) out[j] = res[2 * j];
+    return GP_OK;
+}
+
+}  // extern "C"

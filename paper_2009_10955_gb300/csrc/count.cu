@@ -1,0 +1,434 @@
+// count.cu -- the pattern-count kernel: a persistent, warp-per-task
+// interpreter of the nested-loop search of GraphPi (Sections II-B, IV-B,
+// IV-E), for sm_103a.
+//
+// Work decomposition (Section IV-E, fine-grained tasks + work stealing):
+// every directed CSR entry (v0, v1) is one task that fixes the first two
+// loops. Tasks of all jobs form one global index space; a warp grabs a chunk
+// of consecutive tasks with one atomicAdd on a global cursor, so idle warps
+// take the next work immediately (the device analogue of stealing).
+//
+// Inside a task one warp runs the remaining loops depth-first. Candidate
+// sets are intersections of sorted neighbour lists, clipped to the window the
+// restrictions impose (a restriction becomes a bound on a sorted list, the
+// "break" of Section IV-B). Intersections are warp-cooperative: each lane
+// takes one element of the shorter list and binary-searches it in the longer
+// one, and ballot/popc compacts the matches. The innermost loop is never
+// enumerated: its contribution is the size of its clipped candidate set
+// minus the already-matched vertices inside it.
+//
+// Counts are accumulated per lane in 128 bits and reduced with warp shuffles;
+// one atomic pair (low word, carry into the high word) per warp per job
+// publishes them.
+#include <algorithm>
+#include <climits>
+#include <vector>
+
+#include "engine.h"
+
+namespace gp {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWarps = 8;   // warps per block
+static_assert(sizeof(GpPlan) % 4 == 0, "plan is copied as 32-bit words");
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// First index i in [0, n) with a[i] >= x (n if none).
+__device__ __forceinline__ int lower_bound(const int32_t* __restrict__ a, int n, int x) {
+    int base = 0;
+    while (n > 0) {
+        int half = n >> 1;
+        if (__ldg(a + base + half) < x) { base += half + 1; n -= half + 1; }
+        else n = half;
+    }
+    return base;
+}
+
+struct Acc {   // per-lane 128-bit counter
+    unsigned long long lo = 0, hi = 0;
+    __device__ __forceinline__ void add(unsigned long long x) { lo += x; hi += (lo < x); }
+    __device__ __forceinline__ void sub(unsigned long long x) { hi -= (lo < x); lo -= x; }
+};
+
+__device__ void flush(Acc& acc, unsigned long long* res) {
+    unsigned long long lo = acc.lo, hi = acc.hi;
+    for (int o = 16; o; o >>= 1) {
+        unsigned long long l2 = __shfl_down_sync(kFull, lo, o);
+        unsigned long long h2 = __shfl_down_sync(kFull, hi, o);
+        lo += l2;
+        hi += h2 + (lo < l2);
+    }
+    if ((threadIdx.x & 31) == 0 && (lo | hi)) {
+        unsigned long long old = atomicAdd(res, lo);
+        unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+        if (hi + carry) atomicAdd(res + 1, hi + carry);
+    }
+    acc.lo = acc.hi = 0;
+}
+
+// Warp-cooperative sorted intersection of A and B. Writes the (sorted)
+// result to out when out != nullptr and returns its size (warp-uniform).
+// With acc != nullptr each lane also adds its own matches to acc.
+__device__ __forceinline__ int warp_intersect(const int32_t* __restrict__ A, int na,
+                                              const int32_t* __restrict__ B, int nb,
+                                              int32_t* __restrict__ out, int cap, Acc* acc,
+                                              int lane, int* err, unsigned long long* sbytes) {
+    if (na > nb) {
+        const int32_t* t = A; A = B; B = t;
+        int tn = na; na = nb; nb = tn;
+    }
+    int total = 0, from = 0;
+    for (int base = 0; base < na; base += 32) {
+        int i = base + lane;
+        int x = 0, pos = nb;
+        bool f = false;
+        if (i < na) {
+            x = __ldg(A + i);
+            pos = from + lower_bound(B + from, nb - from, x);
+            f = pos < nb && __ldg(B + pos) == x;
+        }
+        unsigned m = __ballot_sync(kFull, f);
+        if (out && f) {
+            int at = total + __popc(m & lanemask_lt());
+            if (at < cap) out[at] = x; else atomicExch(err, 2);
+        }
+        if (acc && f) acc->add(1);
+        total += __popc(m);
+        int last = min(31, na - 1 - base);
+        from = __shfl_sync(kFull, pos, last);   // later elements are larger
+    }
+    if (sbytes && lane == 0)
+        *sbytes += 4ull * (unsigned long long)(na + nb) + (out ? 4ull * (unsigned long long)total : 0ull);
+    return total;
+}
+
+struct Window { int lo, hi; };   // candidates c with lo < c < hi
+
+__device__ __forceinline__ Window window(uint8_t lo_mask, uint8_t hi_mask, const int* v) {
+    Window w{-1, INT_MAX};
+    for (int j = 0; j < GP_MAX_K; ++j) {
+        if (lo_mask >> j & 1) w.lo = max(w.lo, v[j]);
+        if (hi_mask >> j & 1) w.hi = min(w.hi, v[j]);
+    }
+    return w;
+}
+
+// Clip a sorted list to a window: returns [b, e).
+__device__ __forceinline__ void clip(const int32_t* a, int n, Window w, int& b, int& e) {
+    b = (w.lo < 0) ? 0 : lower_bound(a, n, w.lo + 1);
+    e = (w.hi == INT_MAX) ? n : lower_bound(a, n, w.hi);
+    if (e < b) e = b;
+}
+
+struct TaskCtx {
+    const GpPlan* P;
+    const int64_t* __restrict__ row_ptr;
+    const int32_t* __restrict__ col;
+    int32_t* slots;        // this warp's intermediate sets
+    int slot_cap;
+    int n_vertices;
+    int* slen;             // their lengths (shared memory, per warp)
+    int lane;
+    int* err;
+    unsigned long long* sbytes;   // algorithmic-byte tally (instrumented kernel only)
+};
+
+__device__ __forceinline__ void nbr(const TaskCtx& c, int v, const int32_t*& p, int& n) {
+    int64_t b = __ldg(c.row_ptr + v), e = __ldg(c.row_ptr + v + 1);
+    p = c.col + b;
+    n = (int)(e - b);
+}
+
+__device__ __forceinline__ void run_builds(const TaskCtx& c, int d, const int* v) {
+    const GpLevel& L = c.P->lvl[d];
+    for (int q = 0; q < L.nbuild; ++q) {
+        const GpBuild& B = L.build[q];
+        const int32_t* a; int na;
+        if (B.base_kind == 1) nbr(c, v[B.base], a, na);
+        else { a = c.slots + (size_t)B.base * c.slot_cap; na = c.slen[B.base]; }
+        const int32_t* b; int nb;
+        nbr(c, v[d], b, nb);
+        Window w = window(B.lo_mask, B.hi_mask, v);
+        int a0, a1, b0, b1;
+        clip(a, na, w, a0, a1);
+        clip(b, nb, w, b0, b1);
+        int32_t* out = c.slots + (size_t)B.dst * c.slot_cap;
+        int n = warp_intersect(a + a0, a1 - a0, b + b0, b1 - b0, out, c.slot_cap, nullptr, c.lane, c.err,
+                               c.sbytes);
+        if (c.lane == 0) c.slen[B.dst] = n;
+        __syncwarp();
+    }
+}
+
+// Is x in the sorted list a[0, n)?
+__device__ __forceinline__ bool contains(const int32_t* a, int n, int x) {
+    int p = lower_bound(a, n, x);
+    return p < n && __ldg(a + p) == x;
+}
+
+// Contribution of the innermost loop given v[0..k-2].
+__device__ __forceinline__ void count_last(const TaskCtx& c, const int* v, Acc& acc) {
+    const GpPlan& P = *c.P;
+    const int L = P.k - 1;
+    const GpLevel& lv = P.lvl[L];
+    Window w = window(lv.lo_mask, lv.hi_mask, v);
+    if (P.last_count_only) {
+        const int32_t* a; int na;
+        if (P.last_base_kind == 1) nbr(c, v[P.last_base], a, na);
+        else { a = c.slots + (size_t)P.last_base * c.slot_cap; na = c.slen[P.last_base]; }
+        const int32_t* b; int nb;
+        nbr(c, v[L - 1], b, nb);
+        int a0, a1, b0, b1;
+        clip(a, na, w, a0, a1);
+        clip(b, nb, w, b0, b1);
+        warp_intersect(a + a0, a1 - a0, b + b0, b1 - b0, nullptr, 0, &acc, c.lane, c.err, c.sbytes);
+        // matched vertices inside the intersection are not new vertices
+        bool hit = false;
+        if (c.lane < L && (lv.excl_mask >> c.lane & 1)) {
+            int x = v[c.lane];
+            hit = x > w.lo && x < w.hi && contains(a + a0, a1 - a0, x) && contains(b + b0, b1 - b0, x);
+        }
+        unsigned h = __ballot_sync(kFull, hit);
+        if (c.lane == 0) acc.sub(__popc(h));
+    } else {
+        const int32_t* a; int na;
+        if (lv.src_kind == 1) nbr(c, v[lv.src], a, na);
+        else { a = c.slots + (size_t)lv.src * c.slot_cap; na = c.slen[lv.src]; }
+        int a0, a1;
+        clip(a, na, w, a0, a1);
+        bool hit = false;
+        if (c.lane < L && (lv.excl_mask >> c.lane & 1)) {
+            int x = v[c.lane];
+            hit = x > w.lo && x < w.hi && contains(a + a0, a1 - a0, x);
+        }
+        unsigned h = __ballot_sync(kFull, hit);
+        if (c.lane == 0) acc.add((unsigned long long)(a1 - a0) - __popc(h));
+    }
+}
+
+// Remaining loops of one edge task (v0, v1).
+__device__ void run_task(const TaskCtx& c, int v0, int v1, Acc& acc) {
+    const GpPlan& P = *c.P;
+    const int k = P.k;
+    int v[GP_MAX_K];
+    const int32_t* lst[GP_MAX_K];
+    int cur[GP_MAX_K], end[GP_MAX_K];
+#pragma unroll
+    for (int i = 0; i < GP_MAX_K; ++i) v[i] = -1;
+    v[0] = v0;
+    v[1] = v1;
+    run_builds(c, 1, v);
+    if (k == 3) { count_last(c, v, acc); return; }
+    int d = 2;
+    auto prepare = [&](int dd) {
+        const GpLevel& L = P.lvl[dd];
+        const int32_t* a; int na;
+        if (L.src_kind == 1) nbr(c, v[L.src], a, na);
+        else { a = c.slots + (size_t)L.src * c.slot_cap; na = c.slen[L.src]; }
+        clip(a, na, window(L.lo_mask, L.hi_mask, v), cur[dd], end[dd]);
+        lst[dd] = a;
+    };
+    prepare(2);
+    while (d >= 2) {
+        if (cur[d] >= end[d]) { --d; continue; }
+        int x = __ldg(lst[d] + cur[d]);
+        ++cur[d];
+        if (c.sbytes && c.lane == 0) *c.sbytes += 4;
+        uint8_t ex = P.lvl[d].excl_mask;
+        bool skip = false;
+        for (int j = 0; j < d; ++j) skip |= ((ex >> j) & 1) && v[j] == x;
+        if (skip) continue;
+        v[d] = x;
+        run_builds(c, d, v);
+        if (d == k - 2) count_last(c, v, acc);
+        else { ++d; prepare(d); }
+    }
+}
+
+template <bool kStats>
+__global__ void __launch_bounds__(kWarps * 32)
+k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
+        unsigned long long* __restrict__ cursor, unsigned long long* __restrict__ results,
+        int32_t* __restrict__ slot_pool, int64_t warp_elems, int chunk, long long budget,
+        int* __restrict__ err, unsigned long long* __restrict__ stats) {
+    unsigned long long my_bytes = 0;
+    __shared__ GpPlan s_plan[kWarps];
+    __shared__ int s_len[kWarps][GP_MAX_SLOTS];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * kWarps + w;
+    TaskCtx c;
+    c.P = &s_plan[w];
+    c.slots = slot_pool + gw * warp_elems;
+    c.slen = s_len[w];
+    c.lane = lane;
+    c.err = err;
+    c.row_ptr = nullptr;
+    c.col = nullptr;
+    c.slot_cap = 0;
+    c.n_vertices = 0;
+    c.sbytes = kStats ? &my_bytes : nullptr;
+    int cur_job = -1;
+    int64_t job_lo = 0, job_hi = 0, job_begin = 0;
+    Acc acc;
+    const long long t_start = clock64();
+    for (;;) {
+        if (budget > 0 && clock64() - t_start > budget) break;
+        unsigned long long t0 = 0;
+        if (lane == 0) t0 = atomicAdd(cursor, (unsigned long long)chunk);
+        t0 = __shfl_sync(kFull, t0, 0);
+        if ((int64_t)t0 >= total) break;
+        const int64_t t1 = min((int64_t)t0 + chunk, total);
+        int64_t t = (int64_t)t0;
+        while (t < t1) {
+            if (cur_job < 0 || t < job_lo || t >= job_hi) {
+                int lo = 0, hi = njobs - 1;      // last job whose offset <= t
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (jobs[mid].task_offset <= t) lo = mid; else hi = mid - 1;
+                }
+                if (cur_job >= 0) flush(acc, results + 2 * cur_job);
+                cur_job = lo;
+                const CountJob& J = jobs[lo];
+                const int* src = reinterpret_cast<const int*>(&J.plan);
+                int* dst = reinterpret_cast<int*>(&s_plan[w]);
+                for (int i = lane; i < (int)(sizeof(GpPlan) / 4); i += 32) dst[i] = src[i];
+                __syncwarp();
+                job_lo = J.task_offset;
+                job_hi = J.task_offset + J.ntasks;
+                job_begin = J.task_begin;
+                c.row_ptr = J.row_ptr;
+                c.col = J.col;
+                c.slot_cap = J.slot_cap;
+                c.n_vertices = J.n;
+            }
+            const int64_t tend = min(t1, job_hi);
+            int64_t e = job_begin + (t - job_lo);
+            const int64_t e_end = job_begin + (tend - job_lo);
+            // source vertex of entry e: last u with row_ptr[u] <= e
+            int lo = 0, hi = c.n_vertices - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (__ldg(c.row_ptr + mid) <= e) lo = mid; else hi = mid - 1;
+            }
+            int v0 = lo;
+            int64_t row_end = __ldg(c.row_ptr + v0 + 1);
+            const uint8_t lo1 = s_plan[w].lvl[1].lo_mask & 1, hi1 = s_plan[w].lvl[1].hi_mask & 1;
+            for (; e < e_end; ++e) {
+                while (e >= row_end) { ++v0; row_end = __ldg(c.row_ptr + v0 + 1); }
+                const int v1 = __ldg(c.col + e);
+                if (lo1 && !(v1 > v0)) continue;
+                if (hi1 && !(v1 < v0)) continue;
+                run_task(c, v0, v1, acc);
+            }
+            t = tend;
+        }
+    }
+    if (cur_job >= 0) flush(acc, results + 2 * cur_job);
+    if (kStats && lane == 0 && my_bytes) atomicAdd(stats, my_bytes);
+}
+
+}  // namespace
+
+gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& opt, cudaStream_t st,
+                    uint64_t* results, int64_t* processed, float* kernel_ms, uint64_t* algo_bytes) {
+    if (njobs <= 0) { set_error("no jobs"); return GP_ERR_ARG; }
+    int64_t total = 0;
+    int64_t warp_elems = 1;
+    for (int j = 0; j < njobs; ++j) {
+        total += jobs[j].ntasks;
+        warp_elems = std::max<int64_t>(warp_elems, (int64_t)jobs[j].plan.nslots * jobs[j].slot_cap);
+    }
+    int dev = 0, nsm = 0;
+    GP_CUDA_TRY(cudaGetDevice(&dev));
+    GP_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    int occ = 0;
+    auto kern = opt.stats ? k_count<true> : k_count<false>;
+    GP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWarps * 32, 0));
+    int per_sm = opt.blocks_per_sm > 0 ? std::min(opt.blocks_per_sm, occ) : occ;
+    if (per_sm < 1) per_sm = 1;
+    int64_t blocks = (int64_t)nsm * per_sm;
+    // keep the intermediate-set scratch within a quarter of free memory
+    size_t free_b = 0, total_b = 0;
+    GP_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    const size_t per_block = (size_t)kWarps * (size_t)warp_elems * sizeof(int32_t);
+    while (blocks > nsm && per_block * (size_t)blocks > free_b / 4) blocks -= nsm;
+    if (per_block * (size_t)blocks > free_b / 2) {
+        set_error("intermediate sets need %zu bytes per block; %zu free", per_block, free_b);
+        return GP_ERR_SCRATCH;
+    }
+    int chunk = opt.chunk;
+    if (chunk <= 0) {
+        int64_t per_warp = total / (blocks * kWarps * 64);
+        chunk = (int)std::max<int64_t>(1, std::min<int64_t>(64, per_warp));
+    }
+
+    // device buffers: job table, results (2 per job), cursor, error word
+    const size_t jobs_b = sizeof(CountJob) * (size_t)njobs;
+    const size_t res_b = sizeof(unsigned long long) * (2 * (size_t)njobs + 3);
+    void* d_mem = nullptr;
+    int32_t* d_slots = nullptr;
+    GP_CUDA_TRY(cudaMallocAsync(&d_mem, jobs_b + res_b + 64, st));
+    if (cudaMallocAsync((void**)&d_slots, per_block * (size_t)blocks, st) != cudaSuccess) {
+        cudaFreeAsync(d_mem, st);
+        cudaGetLastError();
+        set_error("cannot allocate %zu bytes of intermediate-set scratch", per_block * (size_t)blocks);
+        return GP_ERR_NOMEM;
+    }
+    CountJob* d_jobs = static_cast<CountJob*>(d_mem);
+    unsigned long long* d_res = reinterpret_cast<unsigned long long*>(static_cast<char*>(d_mem) + jobs_b);
+    unsigned long long* d_cursor = d_res + 2 * njobs;
+    int* d_err = reinterpret_cast<int*>(d_cursor + 1);
+    unsigned long long* d_stats = d_cursor + 2;
+    gp_status rc = GP_OK;
+    std::vector<unsigned long long> h_res(2 * (size_t)njobs + 3, 0);
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (kernel_ms) {
+        GP_CUDA_TRY(cudaEventCreate(&ev0));
+        GP_CUDA_TRY(cudaEventCreate(&ev1));
+    }
+    cudaError_t e = cudaMemcpyAsync(d_jobs, jobs, jobs_b, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_res, 0, res_b, st);
+    if (e == cudaSuccess && ev0) e = cudaEventRecord(ev0, st);
+    if (e == cudaSuccess && total > 0) {
+        kern<<<(unsigned)blocks, kWarps * 32, 0, st>>>(d_jobs, njobs, total, d_cursor, d_res, d_slots,
+                                                      warp_elems, chunk, (long long)opt.budget_cycles,
+                                                      d_err, d_stats);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_res.data(), d_res, res_b, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && ev0) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, ev0, ev1);
+        *kernel_ms = ms;
+    }
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    cudaFreeAsync(d_slots, st);
+    cudaFreeAsync(d_mem, st);
+    if (e != cudaSuccess) {
+        set_error("count kernel failed: %s", cudaGetErrorString(e));
+        return GP_ERR_CUDA;
+    }
+    const int err_word = (int)(h_res[2 * njobs + 1] & 0xffffffffu);
+    if (err_word) {
+        set_error("count kernel reported internal error %d", err_word);
+        return GP_ERR_INTERNAL;
+    }
+    for (int j = 0; j < 2 * njobs; ++j) results[j] = h_res[j];
+    if (algo_bytes) *algo_bytes = h_res[2 * njobs + 2];
+    int64_t done = (int64_t)std::min<unsigned long long>(h_res[2 * njobs], (unsigned long long)total);
+    if (processed) *processed = total == 0 ? 0 : done;
+    return rc;
+}
+
+}  // namespace gp

@@ -1,0 +1,79 @@
+// engine.h -- internal declarations shared by the C ABI and the CUDA code.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <mutex>
+#include <string>
+
+#include "../../include/graphpi.h"
+#include "plan.h"
+
+// The data graph: undirected, simple, sorted adjacency lists in CSR form,
+// resident on one device (Section IV-E keeps the whole graph in memory).
+struct gp_graph {
+    int device = 0;
+    int32_t n = 0;
+    int64_t nnz = 0;              // directed entries = 2 |E|
+    int32_t max_deg = 0;
+    int64_t* row_ptr = nullptr;   // device, n + 1
+    int32_t* col = nullptr;       // device, nnz
+    int32_t* perm = nullptr;      // device, n (new id -> input id) or null
+    std::mutex mu;
+    bool tri_done = false;
+    uint64_t tri_cnt = 0;         // ordered triangles (6 x triangles)
+};
+
+namespace gp {
+
+void set_error(const char* fmt, ...);
+void count_launch(int n = 1);
+
+// Device graph build from m pairs already on the device (graph.cu).
+gp_status build_graph(const int32_t* d_src, const int32_t* d_dst, int64_t m, int32_t n,
+                      bool degree_order, cudaStream_t st, gp_graph* g);
+// Expand a device CSR to pairs (graph.cu).
+gp_status csr_to_pairs(const int64_t* d_row_ptr, const int32_t* d_col, int32_t n, int64_t nnz,
+                       int32_t* d_src, int32_t* d_dst, cudaStream_t st);
+// Maximum degree of a device CSR (graph.cu).
+gp_status max_degree(const int64_t* d_row_ptr, int32_t n, cudaStream_t st, int32_t* out);
+
+// One counting job for the device (count.cu).
+struct CountJob {
+    GpPlan plan;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    int32_t n;
+    int32_t slot_cap;        // elements per intermediate set (>= max degree)
+    int64_t task_begin;      // first CSR entry (edge task) of this job
+    int64_t ntasks;          // edge tasks of this job
+    int64_t task_offset;     // first global task index of this job
+};
+
+struct LaunchOpts {
+    int warps_per_block = 8;
+    int blocks_per_sm = 0;   // 0 = occupancy maximum
+    int chunk = 0;           // 0 = automatic
+    int64_t budget_cycles = 0;
+    bool stats = false;      // instrumented kernel that tallies algorithmic bytes
+};
+
+// Run the jobs in one persistent launch. results[2 j], results[2 j + 1]
+// receive job j's 128-bit count (lo, hi). *processed receives how many
+// global tasks (from 0) were completed (< total only with a budget).
+gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& lo, cudaStream_t st,
+                    uint64_t* results, int64_t* processed, float* kernel_ms = nullptr,
+                    uint64_t* algo_bytes = nullptr);
+
+}  // namespace gp
+
+#define GP_CUDA_TRY(expr)                                                          \
+    do {                                                                           \
+        cudaError_t _e = (expr);                                                   \
+        if (_e != cudaSuccess) {                                                   \
+            gp::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(_e),  \
+                          __FILE__, __LINE__);                                     \
+            return GP_ERR_CUDA;                                                    \
+        }                                                                          \
+    } while (0)

@@ -1,0 +1,52 @@
+// plan.h -- the compiled form of one configuration (schedule + restriction
+// set) that the counting kernel interprets. Shared by the host planner and
+// the device code; plain POD so it can travel as a kernel parameter.
+//
+// Depth d is the position in the schedule (the paper's loop d+1). The
+// candidate set of depth d is the intersection of the neighbour lists of the
+// already-matched pattern neighbours of the depth-d vertex (Section IV-B),
+// built incrementally as its operands become bound (the tmp_AB sets of the
+// House example), clipped to the window that the restrictions impose
+// (a restriction acts as a bound on a sorted candidate list, Section IV-B).
+#pragma once
+#include <stdint.h>
+
+#define GP_MAX_K 7
+#define GP_MAX_SLOTS 16
+#define GP_MAX_BUILDS 8
+
+// One incremental intersection: slot[dst] = base ∩ N(v_d), clipped to the
+// window of the consuming depth that is already known at depth d.
+struct GpBuild {
+    int8_t dst;        // destination slot
+    int8_t base_kind;  // 1: base = N(v_base) ; 2: base = slot[base]
+    int8_t base;
+    uint8_t lo_mask;   // depths j <= d with candidate > v_j
+    uint8_t hi_mask;   // depths j <= d with candidate < v_j
+    int8_t pad[3];
+};
+
+struct GpLevel {
+    int8_t src_kind;   // 0: every vertex (depth 0), 1: N(v_src), 2: slot[src]
+    int8_t src;
+    uint8_t lo_mask;   // candidate > v_j for j in mask (restrictions, closed transitively)
+    uint8_t hi_mask;   // candidate < v_j
+    uint8_t excl_mask; // earlier depths whose vertex may lie in the set (injectivity)
+    int8_t nbuild;     // builds executed after v_d is bound
+    int8_t pad[2];
+    GpBuild build[GP_MAX_BUILDS];
+};
+
+struct GpPlan {
+    int32_t k;
+    int32_t nslots;
+    // 1 when the last depth's final operand is bound at depth k-2: the
+    // intersection base ∩ N(v_{k-2}) is only counted, never stored. The base
+    // is N(v_last_base) (last_base_kind 1) or slot[last_base] (kind 2).
+    int32_t last_count_only;
+    int16_t last_base_kind;
+    int16_t last_base;
+    int8_t order[GP_MAX_K];   // pattern vertex searched at depth d
+    int8_t pad[1];
+    GpLevel lvl[GP_MAX_K];
+};

@@ -1,0 +1,103 @@
+"""CPU-side checks of the library: every symbol the header declares is
+exported, and the host planner (automorphisms, Algorithm 1, schedules,
+performance model) agrees exactly with the oracle's restatement."""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import planner_ref as pr
+from synth import named_pattern, random_pattern_set
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def N():
+    from paper_2009_10955_gb300 import native
+    return native()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "graphpi.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gp_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol(N):
+    names = declared_functions()
+    assert len(names) >= 20
+    lib = N.lib()
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(N.SIGNATURES)
+
+
+PATTERNS = ["triangle", "c4", "house", "k4", "c5", "diamond", "k6e", "c6chord", "grid3x2",
+            "tailed_triangle", "path4", "star4"]
+
+
+@pytest.mark.parametrize("name", PATTERNS)
+def test_planner_matches_oracle(N, name):
+    adj = named_pattern(name)
+    p = N.gp_pattern_create(adj)
+    assert p.aut_count() == len(pr.automorphisms(adj.tolist()))
+    assert set(p.restriction_sets()) == set(pr.restriction_sets(adj.tolist()))
+    sc, kp = p.schedules()
+    rsc, rkp = pr.efficient_schedules(adj.tolist())
+    assert sc == list(rsc) and kp == rkp
+
+
+@pytest.mark.parametrize("name", ["triangle", "house", "k4", "c5", "k6e", "grid3x2"])
+def test_cost_model_matches_oracle(N, name):
+    adj = named_pattern(name)
+    p = N.gp_pattern_create(adj)
+    sets = pr.restriction_sets(adj.tolist())
+    scheds, _ = pr.efficient_schedules(adj.tolist())
+    for V, E, T in [(2000.0, 19905.0, 6 * 1301.0), (1048576.0, 15700364.0, 6.0e9), (10.0, 20.0, 0.0)]:
+        for s in scheds[:12]:
+            for r in sets[:12]:
+                a = N.gp_config_cost(p, s, r, V, E, T)
+                b = pr.cost(adj.tolist(), s, r, V, E, T)
+                assert abs(a - b) <= 1e-12 * max(abs(b), 1e-300)
+
+
+def test_random_patterns_planner(N):
+    for adj in random_pattern_set(12, 3, 5, 0.5, seed=5):
+        p = N.gp_pattern_create(adj)
+        assert set(p.restriction_sets()) == set(pr.restriction_sets(adj.tolist()))
+        assert p.schedules()[0] == list(pr.efficient_schedules(adj.tolist())[0])
+
+
+def test_schedule_top_k_is_sorted_by_cost(N):
+    p = N.gp_pattern_create(named_pattern("house"))
+    s = N.gp_schedule(p, None, top_k=5)
+    costs = [s.get(i)[2] for i in range(len(s))]
+    assert costs == sorted(costs)
+    rows = pr.all_configurations(named_pattern("house").tolist(), float(1 << 20), 8.0 * (1 << 20),
+                                 6.0 * 8.0 * (1 << 20))
+    assert abs(costs[0] - rows[0][0]) <= 1e-12 * rows[0][0]
+
+
+def test_bad_patterns_rejected(N):
+    bad = [np.zeros((2, 2), np.uint8),                      # too small
+           np.zeros((8, 8), np.uint8),                      # too large
+           np.array([[0, 1, 0], [0, 0, 1], [0, 1, 0]], np.uint8),   # asymmetric
+           np.array([[1, 1, 0], [1, 0, 1], [0, 1, 0]], np.uint8),   # self loop
+           np.array([[0, 1, 0, 0], [1, 0, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0]], np.uint8)]  # disconnected
+    for adj in bad:
+        with pytest.raises(N.GraphPiError) as e:
+            N.gp_pattern_create(adj)
+        assert e.value.status == N.GP_ERR_PATTERN
+
+
+def test_explicit_schedule_validation(N):
+    p = N.gp_pattern_create(named_pattern("triangle"))
+    with pytest.raises(N.GraphPiError):
+        N.gp_schedule_explicit(p, (0, 1, 2), [(0, 1)])         # leaves 3 of 6 orders: invalid
+    N.gp_schedule_explicit(p, (0, 1, 2), [(0, 1), (1, 2)])
+    c4 = N.gp_pattern_create(named_pattern("c4"))
+    with pytest.raises(N.GraphPiError):
+        N.gp_schedule_explicit(c4, (0, 2, 1, 3), [(0, 1), (0, 2), (1, 3)])  # disconnected prefix

@@ -1,0 +1,73 @@
+"""The multi-GPU path's host logic on CPU: world-size-2 gloo ranks shard the
+edge tasks and sum partial counts exactly (the sharded path's one exchange).
+Partial counts come from the oracle's restricted enumeration per root range,
+so the test needs no GPU."""
+
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+import oracle
+from oracle import planner_ref as pr
+from synth import er_edges, named_pattern
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, q):
+    import torch.distributed as dist
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    n = 120
+    s, d = er_edges(n, 900, seed=21)
+    g = oracle.build_csr(n, s, d)
+    lo, hi = bench.shard_range(n, rank, world)           # rows of this rank
+    parts = []
+    for name in ("triangle", "house", "c4"):
+        adj = named_pattern(name)
+        sched, _ = pr.efficient_schedules(adj.tolist())
+        rs = pr.restriction_sets(adj.tolist())[0]
+        parts.append(oracle.count_restricted(adj, sched[0], rs, g, root_begin=lo, root_end=hi, threads=1))
+    # a value above 2^32 exercises the carry between halves
+    parts.append((1 << 33) + rank * ((1 << 32) - 1))
+    total = bench.allreduce_counts(parts)
+    q.put((rank, total))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_shard_and_exact_sum():
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    n = 120
+    s, d = er_edges(n, 900, seed=21)
+    g = oracle.build_csr(n, s, d)
+    expect = [oracle.count(named_pattern(x), g) for x in ("triangle", "house", "c4")]
+    expect.append(2 * (1 << 33) + ((1 << 32) - 1))
+    assert res[0] == res[1] == expect
+
+
+def test_shard_ranges_partition():
+    import bench
+    for ntasks in (0, 1, 7, 1000, 31400728):
+        for world in (1, 2, 3, 8):
+            rs = [bench.shard_range(ntasks, r, world) for r in range(world)]
+            assert rs[0][0] == 0 and rs[-1][1] == ntasks
+            assert all(a[1] == b[0] for a, b in zip(rs, rs[1:]))
