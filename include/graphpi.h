@@ -218,6 +218,26 @@ gp_status gp_count_batch(gp_graph* const* graphs, const gp_schedules* const* sch
                          const int32_t* idx, int32_t njobs, const gp_count_opts* opts,
                          void* stream, uint64_t* out);
 
+/* Time-sliced batch: like gp_count_batch, but job j covers only its edge
+ * tasks [task_begin[j], task_end[j]) (task_end[j] <= 0 means all) and
+ * opts->budget_cycles may stop the launch early. Work items are handed out
+ * in job order, so a stopped launch leaves every job with a processed
+ * prefix: out[j] receives the count over that prefix and next_task[j] the
+ * first unprocessed task (== the job's end when it is complete). Returns
+ * GP_OK when every job completed, GP_PARTIAL otherwise; counts over disjoint
+ * task ranges add up to the full count. Synchronises `stream`. This is the
+ * call a continuous-batching server issues once per time slice. */
+gp_status gp_count_batch_ranges(gp_graph* const* graphs, const gp_schedules* const* scheds,
+                                const int32_t* idx, const int64_t* task_begin,
+                                const int64_t* task_end, int32_t njobs,
+                                const gp_count_opts* opts, void* stream, uint64_t* out,
+                                int64_t* next_task);
+
+/* Device scratch (bytes) a gp_count of plan idx on g allocates for its
+ * intermediate sets with the given options (for admission control). */
+gp_status gp_count_scratch_bytes(const gp_graph* g, const gp_schedules* s, int32_t idx,
+                                 const gp_count_opts* opts, uint64_t* bytes);
+
 /* ------------------------------------------------------------------ misc */
 
 const char* gp_status_str(gp_status s);

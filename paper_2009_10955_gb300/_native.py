@@ -52,6 +52,8 @@ SIGNATURES = {
     "gp_schedule_destroy": (None, [P]),
     "gp_count": (i32, [P, P, i32, P, P, P]),
     "gp_count_batch": (i32, [P, P, P, i32, P, P, P]),
+    "gp_count_batch_ranges": (i32, [P, P, P, P, P, i32, P, P, P, P]),
+    "gp_count_scratch_bytes": (i32, [P, P, i32, P, P]),
     "gp_status_str": (ctypes.c_char_p, [i32]),
     "gp_last_error": (ctypes.c_char_p, []),
     "gp_take_launch_count": (i64, []),
@@ -206,6 +208,29 @@ def gp_count_batch(graphs, schedules, idx=None, opts=None, stream=None):
     check(lib().gp_count_batch(G, S, _ptr(I), n, ctypes.byref(opts) if opts is not None else None,
                                _stream(stream), _ptr(out)), "gp_count_batch")
     return out
+
+
+def gp_count_batch_ranges(graphs, schedules, idx, task_begin, task_end, opts=None, stream=None):
+    """Returns (status, counts, next_task) for one time slice."""
+    n = len(graphs)
+    G = (ctypes.c_void_p * n)(*[g.h.value for g in graphs])
+    S = (ctypes.c_void_p * n)(*[s.h.value for s in schedules])
+    I = np.ascontiguousarray(idx, dtype=np.int32)
+    B = np.ascontiguousarray(task_begin, dtype=np.int64)
+    E = np.ascontiguousarray(task_end, dtype=np.int64)
+    out = np.zeros(n, dtype=np.uint64)
+    nxt = np.zeros(n, dtype=np.int64)
+    st = check(lib().gp_count_batch_ranges(G, S, _ptr(I), _ptr(B), _ptr(E), n,
+                                           ctypes.byref(opts) if opts is not None else None,
+                                           _stream(stream), _ptr(out), _ptr(nxt)), "gp_count_batch_ranges")
+    return st, out, nxt
+
+
+def gp_count_scratch_bytes(graph, schedules, idx=0, opts=None):
+    out = ctypes.c_uint64()
+    check(lib().gp_count_scratch_bytes(graph.h, schedules.h, idx, ctypes.byref(opts) if opts is not None else None,
+                                       ctypes.byref(out)), "gp_count_scratch_bytes")
+    return out.value
 
 
 def gp_config_cost(pattern, order, restrictions, n_vertices, n_edges, tri_cnt):

@@ -511,4 +511,59 @@ gp_status gp_count_batch(gp_graph* const* graphs, const gp_schedules* const* sch
     return GP_OK;
 }
 
+gp_status gp_count_batch_ranges(gp_graph* const* graphs, const gp_schedules* const* scheds,
+                                const int32_t* idx, const int64_t* task_begin,
+                                const int64_t* task_end, int32_t njobs,
+                                const gp_count_opts* opts, void* stream, uint64_t* out,
+                                int64_t* next_task) {
+    if (!graphs || !scheds || !out || !next_task || njobs < 1) return fail(GP_ERR_ARG, "bad argument");
+    if (!opts_ok(opts)) return fail(GP_ERR_ARG, "gp_count_opts.struct_size mismatch");
+    std::vector<CountJob> jobs((size_t)njobs);
+    int64_t off = 0;
+    for (int32_t j = 0; j < njobs; ++j) {
+        gp_count_opts r;
+        std::memset(&r, 0, sizeof(r));
+        r.struct_size = sizeof(r);
+        r.task_begin = task_begin ? task_begin[j] : 0;
+        r.task_end = task_end ? task_end[j] : 0;
+        gp_status rc = make_job(graphs[j], scheds[j], idx ? idx[j] : 0, &r, &jobs[j]);
+        if (rc != GP_OK) return rc;
+        if (graphs[j]->device != graphs[0]->device) return fail(GP_ERR_ARG, "graphs on different devices");
+        jobs[j].task_offset = off;
+        off += jobs[j].ntasks;
+    }
+    gp_status rc = ensure_device(graphs[0]);
+    if (rc != GP_OK) return rc;
+    std::vector<uint64_t> res(2 * (size_t)njobs, 0);
+    int64_t done = 0;
+    float ms = 0.f;
+    const bool want_ms = opts && opts->kernel_ms;
+    rc = run_count(jobs.data(), njobs, launch_opts(opts), static_cast<cudaStream_t>(stream), res.data(),
+                   &done, want_ms ? &ms : nullptr, nullptr);
+    if (rc != GP_OK) return rc;
+    for (int32_t j = 0; j < njobs; ++j)
+        if (res[2 * j + 1]) return fail(GP_ERR_OVERFLOW, "a count does not fit in 64 bits");
+    bool all = true;
+    for (int32_t j = 0; j < njobs; ++j) {
+        int64_t p = std::min(std::max<int64_t>(done - jobs[j].task_offset, 0), jobs[j].ntasks);
+        out[j] = res[2 * j];
+        next_task[j] = jobs[j].task_begin + p;
+        all = all && p == jobs[j].ntasks;
+    }
+    if (want_ms) *opts->kernel_ms = ms;
+    return all ? GP_OK : GP_PARTIAL;
+}
+
+gp_status gp_count_scratch_bytes(const gp_graph* g, const gp_schedules* s, int32_t idx,
+                                 const gp_count_opts* opts, uint64_t* bytes) {
+    if (!g || !s || !bytes) return fail(GP_ERR_ARG, "null argument");
+    if (idx < 0 || idx >= (int32_t)s->plans.size()) return fail(GP_ERR_ARG, "plan index out of range");
+    if (!opts_ok(opts)) return fail(GP_ERR_ARG, "gp_count_opts.struct_size mismatch");
+    CountJob job;
+    std::memset(&job, 0, sizeof(job));
+    job.plan = s->plans[idx];
+    job.slot_cap = g->max_deg > 0 ? g->max_deg : 1;
+    return scratch_bytes(&job, 1, launch_opts(opts), bytes);
+}
+
 }  // extern "C"

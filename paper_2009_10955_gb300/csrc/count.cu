@@ -51,6 +51,18 @@ __device__ __forceinline__ int lower_bound(const int32_t* __restrict__ a, int n,
     return base;
 }
 
+// Algorithmic bytes of intersecting sorted lists of lengths na and nb: the
+// cheaper of a merge (4 bytes per element of both) and a binary search of
+// each element of the shorter list in the longer one, counted in 32-byte
+// sectors (eight ids per sector, so about log2(n / 8) + 1 sectors a search).
+__device__ __forceinline__ unsigned long long intersect_bytes(int na, int nb) {
+    const int sh = min(na, nb), lo = max(na, nb);
+    const unsigned long long merge = 4ull * (unsigned long long)(na + nb);
+    const int sectors = (lo > 8) ? (32 - __clz((lo >> 3) | 1)) + 1 : 1;
+    const unsigned long long search = (unsigned long long)sh * (4ull + 32ull * (unsigned long long)sectors);
+    return merge < search ? merge : search;
+}
+
 struct Acc {   // per-lane 128-bit counter
     unsigned long long lo = 0, hi = 0;
     __device__ __forceinline__ void add(unsigned long long x) { lo += x; hi += (lo < x); }
@@ -105,7 +117,7 @@ __device__ __forceinline__ int warp_intersect(const int32_t* __restrict__ A, int
         from = __shfl_sync(kFull, pos, last);   // later elements are larger
     }
     if (sbytes && lane == 0)
-        *sbytes += 4ull * (unsigned long long)(na + nb) + (out ? 4ull * (unsigned long long)total : 0ull);
+        *sbytes += intersect_bytes(na, nb) + (out ? 4ull * (unsigned long long)total : 0ull);
     return total;
 }
 
@@ -213,6 +225,125 @@ __device__ __forceinline__ void count_last(const TaskCtx& c, const int* v, Acc& 
     }
 }
 
+// Per-lane sorted intersection size: binary search of the shorter list in
+// the longer when their lengths differ a lot, a linear merge otherwise.
+__device__ __forceinline__ int lane_intersect_count(const int32_t* __restrict__ A, int na,
+                                                    const int32_t* __restrict__ B, int nb) {
+    if (na > nb) {
+        const int32_t* t = A; A = B; B = t;
+        int tn = na; na = nb; nb = tn;
+    }
+    int cnt = 0;
+    if (na == 0) return 0;
+    if (nb > 16 * na) {
+        int from = 0;
+        for (int i = 0; i < na && from < nb; ++i) {
+            int x = __ldg(A + i);
+            from += lower_bound(B + from, nb - from, x);
+            cnt += (from < nb && __ldg(B + from) == x);
+        }
+        return cnt;
+    }
+    int i = 0, j = 0;
+    int x = __ldg(A), y = __ldg(B);
+    for (;;) {
+        if (x == y) {
+            ++cnt;
+            if (++i == na || ++j == nb) break;
+            x = __ldg(A + i);
+            y = __ldg(B + j);
+        } else if (x < y) {
+            if (++i == na) break;
+            x = __ldg(A + i);
+        } else {
+            if (++j == nb) break;
+            y = __ldg(B + j);
+        }
+    }
+    return cnt;
+}
+
+// Work above which a lane hands its last-level count to the whole warp.
+constexpr int kLaneWork = 192;
+
+// Per-lane version of count_last: v[] is this lane's own matched vertices.
+// Returns false (and counts nothing) when the work is large enough that the
+// warp-cooperative count_last should take it.
+__device__ __forceinline__ bool count_last_lane(const TaskCtx& c, const int* v, Acc& acc) {
+    const GpPlan& P = *c.P;
+    const int L = P.k - 1;
+    const GpLevel& lv = P.lvl[L];
+    Window w = window(lv.lo_mask, lv.hi_mask, v);
+    if (P.last_count_only) {
+        const int32_t* a; int na;
+        if (P.last_base_kind == 1) nbr(c, v[P.last_base], a, na);
+        else { a = c.slots + (size_t)P.last_base * c.slot_cap; na = c.slen[P.last_base]; }
+        const int32_t* b; int nb;
+        nbr(c, v[L - 1], b, nb);
+        int a0, a1, b0, b1;
+        clip(a, na, w, a0, a1);
+        clip(b, nb, w, b0, b1);
+        const int la = a1 - a0, lb = b1 - b0;
+        const int sh = min(la, lb), lo = max(la, lb);
+        const int work = (lo > 16 * sh) ? sh * (32 - __clz(lo | 1)) : la + lb;
+        if (work > kLaneWork) return false;
+        int cnt = lane_intersect_count(a + a0, la, b + b0, lb);
+        for (int j = 0; j < L; ++j) {
+            if (!(lv.excl_mask >> j & 1)) continue;
+            int x = v[j];
+            if (x > w.lo && x < w.hi && contains(a + a0, la, x) && contains(b + b0, lb, x)) --cnt;
+        }
+        acc.add((unsigned long long)cnt);
+        if (c.sbytes) *c.sbytes += intersect_bytes(la, lb);
+        return true;
+    }
+    const int32_t* a; int na;
+    if (lv.src_kind == 1) nbr(c, v[lv.src], a, na);
+    else { a = c.slots + (size_t)lv.src * c.slot_cap; na = c.slen[lv.src]; }
+    int a0, a1;
+    clip(a, na, w, a0, a1);
+    int cnt = a1 - a0;
+    for (int j = 0; j < L; ++j) {
+        if (!(lv.excl_mask >> j & 1)) continue;
+        int x = v[j];
+        if (x > w.lo && x < w.hi && contains(a + a0, a1 - a0, x)) --cnt;
+    }
+    acc.add((unsigned long long)cnt);
+    return true;
+}
+
+// The loop at depth k-2 with one candidate per lane: every lane counts the
+// last level for its own candidate; candidates with heavy intersections are
+// then counted one at a time by the whole warp.
+__device__ __forceinline__ void lane_parallel_last_two(const TaskCtx& c, int* v, const int32_t* lst,
+                                                       int beg, int end, Acc& acc) {
+    const GpPlan& P = *c.P;
+    const int d = P.k - 2;
+    const uint8_t ex = P.lvl[d].excl_mask;
+    for (int base = beg; base < end; base += 32) {
+        const int i = base + c.lane;
+        int x = -1;
+        bool active = i < end;
+        if (active) {
+            x = __ldg(lst + i);
+            for (int j = 0; j < d; ++j) active &= !(((ex >> j) & 1) && v[j] == x);
+            if (c.sbytes) *c.sbytes += 4;
+        }
+        bool deferred = false;
+        if (active) {
+            v[d] = x;
+            deferred = !count_last_lane(c, v, acc);
+        }
+        unsigned dm = __ballot_sync(kFull, deferred);
+        while (dm) {
+            const int src = __ffs(dm) - 1;
+            dm &= dm - 1;
+            v[d] = __shfl_sync(kFull, x, src);
+            count_last(c, v, acc);
+        }
+    }
+}
+
 // Remaining loops of one edge task (v0, v1).
 __device__ void run_task(const TaskCtx& c, int v0, int v1, Acc& acc) {
     const GpPlan& P = *c.P;
@@ -235,8 +366,14 @@ __device__ void run_task(const TaskCtx& c, int v0, int v1, Acc& acc) {
         clip(a, na, window(L.lo_mask, L.hi_mask, v), cur[dd], end[dd]);
         lst[dd] = a;
     };
+    const bool lane_last = P.lvl[k - 2].nbuild == 0;
     prepare(2);
     while (d >= 2) {
+        if (lane_last && d == k - 2) {
+            lane_parallel_last_two(c, v, lst[d], cur[d], end[d], acc);
+            --d;
+            continue;
+        }
         if (cur[d] >= end[d]) { --d; continue; }
         int x = __ldg(lst[d] + cur[d]);
         ++cur[d];
@@ -252,8 +389,8 @@ __device__ void run_task(const TaskCtx& c, int v0, int v1, Acc& acc) {
     }
 }
 
-template <bool kStats>
-__global__ void __launch_bounds__(kWarps * 32)
+template <bool kStats, int kMinBlocks>
+__global__ void __launch_bounds__(kWarps * 32, kMinBlocks)
 k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
         unsigned long long* __restrict__ cursor, unsigned long long* __restrict__ results,
         int32_t* __restrict__ slot_pool, int64_t warp_elems, int chunk, long long budget,
@@ -320,49 +457,127 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
             int v0 = lo;
             int64_t row_end = __ldg(c.row_ptr + v0 + 1);
             const uint8_t lo1 = s_plan[w].lvl[1].lo_mask & 1, hi1 = s_plan[w].lvl[1].hi_mask & 1;
-            for (; e < e_end; ++e) {
-                while (e >= row_end) { ++v0; row_end = __ldg(c.row_ptr + v0 + 1); }
-                const int v1 = __ldg(c.col + e);
-                if (lo1 && !(v1 > v0)) continue;
-                if (hi1 && !(v1 < v0)) continue;
-                run_task(c, v0, v1, acc);
+            if (s_plan[w].k == 3 && s_plan[w].lvl[1].nbuild == 0) {
+                // one task per lane; heavy ones go to the whole warp
+                int v[GP_MAX_K];
+#pragma unroll
+                for (int i = 0; i < GP_MAX_K; ++i) v[i] = -1;
+                for (int64_t eb = e; eb < e_end; eb += 32) {
+                    const int64_t my = eb + lane;
+                    bool active = my < e_end;
+                    int a0 = -1, a1 = -1;
+                    if (active) {
+                        int rl = v0, rh = c.n_vertices - 1;     // row of entry `my`
+                        while (rl < rh) {
+                            int mid = (rl + rh + 1) >> 1;
+                            if (__ldg(c.row_ptr + mid) <= my) rl = mid; else rh = mid - 1;
+                        }
+                        a0 = rl;
+                        a1 = __ldg(c.col + my);
+                        if (lo1 && !(a1 > a0)) active = false;
+                        if (hi1 && !(a1 < a0)) active = false;
+                    }
+                    bool deferred = false;
+                    if (active) {
+                        v[0] = a0;
+                        v[1] = a1;
+                        deferred = !count_last_lane(c, v, acc);
+                    }
+                    unsigned dm = __ballot_sync(kFull, deferred);
+                    while (dm) {
+                        const int src = __ffs(dm) - 1;
+                        dm &= dm - 1;
+                        v[0] = __shfl_sync(kFull, a0, src);
+                        v[1] = __shfl_sync(kFull, a1, src);
+                        count_last(c, v, acc);
+                    }
+                }
+            } else {
+                for (; e < e_end; ++e) {
+                    while (e >= row_end) { ++v0; row_end = __ldg(c.row_ptr + v0 + 1); }
+                    const int v1 = __ldg(c.col + e);
+                    if (lo1 && !(v1 > v0)) continue;
+                    if (hi1 && !(v1 < v0)) continue;
+                    run_task(c, v0, v1, acc);
+                }
             }
             t = tend;
         }
     }
     if (cur_job >= 0) flush(acc, results + 2 * cur_job);
-    if (kStats && lane == 0 && my_bytes) atomicAdd(stats, my_bytes);
+    if (kStats) {
+        for (int o = 16; o; o >>= 1) my_bytes += __shfl_down_sync(kFull, my_bytes, o);
+        if (lane == 0 && my_bytes) atomicAdd(stats, my_bytes);
+    }
 }
 
 }  // namespace
 
-gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& opt, cudaStream_t st,
-                    uint64_t* results, int64_t* processed, float* kernel_ms, uint64_t* algo_bytes) {
-    if (njobs <= 0) { set_error("no jobs"); return GP_ERR_ARG; }
-    int64_t total = 0;
-    int64_t warp_elems = 1;
+namespace {
+
+using KernelFn = void (*)(const CountJob*, int, int64_t, unsigned long long*, unsigned long long*,
+                          int32_t*, int64_t, int, long long, int*, unsigned long long*);
+
+struct Geometry {
+    KernelFn kern;
+    int64_t blocks;
+    int64_t warp_elems;     // scratch elements per warp
+    size_t per_block;       // scratch bytes per block
+    int64_t total;          // tasks over all jobs
+};
+
+// Grid of the persistent launch: SM count x resident blocks per SM, reduced
+// (in whole waves of SMs) until the per-warp intermediate-set scratch fits in
+// a quarter of the free device memory.
+gp_status geometry(const CountJob* jobs, int njobs, const LaunchOpts& opt, Geometry* g) {
+    g->total = 0;
+    g->warp_elems = 1;
     for (int j = 0; j < njobs; ++j) {
-        total += jobs[j].ntasks;
-        warp_elems = std::max<int64_t>(warp_elems, (int64_t)jobs[j].plan.nslots * jobs[j].slot_cap);
+        g->total += jobs[j].ntasks;
+        g->warp_elems = std::max<int64_t>(g->warp_elems, (int64_t)jobs[j].plan.nslots * jobs[j].slot_cap);
     }
     int dev = 0, nsm = 0;
     GP_CUDA_TRY(cudaGetDevice(&dev));
     GP_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     int occ = 0;
-    auto kern = opt.stats ? k_count<true> : k_count<false>;
-    GP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWarps * 32, 0));
+    // two register budgets: about 96 registers (2 blocks per SM) or 64 (4)
+    const bool dense = opt.blocks_per_sm >= 3;
+    g->kern = opt.stats ? (dense ? k_count<true, 4> : k_count<true, 1>)
+                        : (dense ? k_count<false, 4> : k_count<false, 1>);
+    GP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, g->kern, kWarps * 32, 0));
     int per_sm = opt.blocks_per_sm > 0 ? std::min(opt.blocks_per_sm, occ) : occ;
     if (per_sm < 1) per_sm = 1;
-    int64_t blocks = (int64_t)nsm * per_sm;
-    // keep the intermediate-set scratch within a quarter of free memory
+    g->blocks = (int64_t)nsm * per_sm;
     size_t free_b = 0, total_b = 0;
     GP_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-    const size_t per_block = (size_t)kWarps * (size_t)warp_elems * sizeof(int32_t);
-    while (blocks > nsm && per_block * (size_t)blocks > free_b / 4) blocks -= nsm;
-    if (per_block * (size_t)blocks > free_b / 2) {
-        set_error("intermediate sets need %zu bytes per block; %zu free", per_block, free_b);
+    g->per_block = (size_t)kWarps * (size_t)g->warp_elems * sizeof(int32_t);
+    while (g->blocks > nsm && g->per_block * (size_t)g->blocks > free_b / 4) g->blocks -= nsm;
+    if (g->per_block * (size_t)g->blocks > free_b / 2) {
+        set_error("intermediate sets need %zu bytes per block; %zu free", g->per_block, free_b);
         return GP_ERR_SCRATCH;
     }
+    return GP_OK;
+}
+
+}  // namespace
+
+gp_status scratch_bytes(const CountJob* jobs, int njobs, const LaunchOpts& opt, uint64_t* bytes) {
+    Geometry g;
+    gp_status rc = geometry(jobs, njobs, opt, &g);
+    if (rc != GP_OK) return rc;
+    *bytes = (uint64_t)g.per_block * (uint64_t)g.blocks;
+    return GP_OK;
+}
+
+gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& opt, cudaStream_t st,
+                    uint64_t* results, int64_t* processed, float* kernel_ms, uint64_t* algo_bytes) {
+    if (njobs <= 0) { set_error("no jobs"); return GP_ERR_ARG; }
+    Geometry geo;
+    gp_status grc = geometry(jobs, njobs, opt, &geo);
+    if (grc != GP_OK) return grc;
+    const int64_t total = geo.total, blocks = geo.blocks, warp_elems = geo.warp_elems;
+    const size_t per_block = geo.per_block;
+    auto kern = geo.kern;
     int chunk = opt.chunk;
     if (chunk <= 0) {
         int64_t per_warp = total / (blocks * kWarps * 64);

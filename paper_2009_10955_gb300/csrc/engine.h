@@ -66,6 +66,9 @@ gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& lo, cudaS
                     uint64_t* results, int64_t* processed, float* kernel_ms = nullptr,
                     uint64_t* algo_bytes = nullptr);
 
+// Device scratch run_count would allocate for these jobs and options.
+gp_status scratch_bytes(const CountJob* jobs, int njobs, const LaunchOpts& lo, uint64_t* bytes);
+
 }  // namespace gp
 
 #define GP_CUDA_TRY(expr)                                                          \

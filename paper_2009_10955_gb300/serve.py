@@ -1,0 +1,168 @@
+"""Continuous-batching server for pattern-count queries on device-resident
+graphs.
+
+Requests (graph name, pattern) arrive at any time. The server keeps the
+graphs and the plans on the device and runs in time slices: each slice is
+ONE persistent launch (``gp_count_batch_ranges``) over every admitted job,
+cut off after ``slice_cycles`` device cycles. Between slices, finished jobs
+leave, their results are published, and requests that arrived meanwhile are
+admitted as long as the slice's intermediate-set scratch stays within the
+memory budget. A job's partial counts over disjoint task ranges add up to
+its exact count, so a job may span any number of slices.
+
+The scheduling here is host-side bookkeeping; all counting runs in the
+library's kernels.
+"""
+
+import collections
+import threading
+import time
+
+import numpy as np
+
+from . import _native as N
+
+
+class Request:
+    __slots__ = ("rid", "graph", "adj", "arrival", "done", "count", "error", "finish", "sched",
+                 "next_task", "end_task", "acc", "slices", "scratch")
+
+    def __init__(self, rid, graph, adj, arrival):
+        self.rid = rid
+        self.graph = graph
+        self.adj = np.ascontiguousarray(adj, dtype=np.uint8)
+        self.arrival = arrival
+        self.done = threading.Event()
+        self.count = None
+        self.error = None
+        self.finish = None
+        self.sched = None
+        self.next_task = 0
+        self.end_task = 0
+        self.acc = 0
+        self.slices = 0
+        self.scratch = 0
+
+    @property
+    def latency(self):
+        return None if self.finish is None else self.finish - self.arrival
+
+
+class Server:
+    """Continuous batching over device-resident graphs (see module doc)."""
+
+    def __init__(self, graphs, slice_ms=20.0, max_batch=256, mem_budget=None, stream=None,
+                 clock_ghz=1.9, max_slices=None):
+        self.graphs = dict(graphs)
+        self.slice_cycles = int(slice_ms * 1e-3 * clock_ghz * 1e9)
+        self.max_batch = max_batch
+        self.mem_budget = mem_budget
+        self.stream = stream
+        self.max_slices = max_slices
+        self._plans = {}
+        self._pending = collections.deque()
+        self._active = []
+        self._cv = threading.Condition()
+        self._stop = False
+        self._rid = 0
+        self._nnz = {k: g.device_csr()[2] for k, g in self.graphs.items()}
+        self.slices = 0
+        self.thread = threading.Thread(target=self._loop, daemon=True)
+        self.thread.start()
+
+    # ------------------------------------------------------------ client side
+    def submit(self, graph, adj, arrival=None):
+        with self._cv:
+            self._rid += 1
+            r = Request(self._rid, graph, adj, time.perf_counter() if arrival is None else arrival)
+            self._pending.append(r)
+            self._cv.notify()
+        return r
+
+    def close(self):
+        with self._cv:
+            self._stop = True
+            self._cv.notify()
+        self.thread.join()
+
+    # ------------------------------------------------------------ server side
+    def _plan(self, graph, adj):
+        key = (graph, adj.tobytes(), adj.shape[0])
+        s = self._plans.get(key)
+        if s is None:
+            g = self.graphs[graph]
+            s = N.gp_schedule(N.gp_pattern_create(adj), g, top_k=1, stream=self.stream)
+            self._plans[key] = s
+        return s
+
+    def _admit(self):
+        """Move pending requests into the active set while the batch's
+        scratch (the maximum over its jobs) fits the memory budget."""
+        while self._pending and len(self._active) < self.max_batch:
+            r = self._pending[0]
+            try:
+                r.sched = self._plan(r.graph, r.adj)
+                r.scratch = N.gp_count_scratch_bytes(self.graphs[r.graph], r.sched, 0)
+            except Exception as e:  # bad pattern or graph: answer with the error
+                self._pending.popleft()
+                r.error = e
+                r.finish = time.perf_counter()
+                r.done.set()
+                continue
+            need = max([a.scratch for a in self._active] + [r.scratch])
+            if self.mem_budget is not None and self._active and need > self.mem_budget:
+                break
+            self._pending.popleft()
+            r.next_task, r.end_task = 0, self._nnz[r.graph]
+            self._active.append(r)
+
+    def _loop(self):
+        while True:
+            with self._cv:
+                while not self._stop and not self._pending and not self._active:
+                    self._cv.wait()
+                if self._stop and not self._pending and not self._active:
+                    return
+                self._admit()
+                batch = list(self._active)
+            if not batch:
+                continue
+            opts = N.make_opts(budget_cycles=self.slice_cycles)
+            try:
+                st, out, nxt = N.gp_count_batch_ranges(
+                    [self.graphs[r.graph] for r in batch], [r.sched for r in batch],
+                    [0] * len(batch), [r.next_task for r in batch], [r.end_task for r in batch],
+                    opts, stream=self.stream)
+            except Exception as e:
+                now = time.perf_counter()
+                with self._cv:
+                    for r in batch:
+                        r.error, r.finish = e, now
+                        r.done.set()
+                    self._active = []
+                continue
+            self.slices += 1
+            now = time.perf_counter()
+            with self._cv:
+                still = []
+                for r, c, t in zip(batch, out, nxt):
+                    r.acc += int(c)
+                    r.next_task = int(t)
+                    r.slices += 1
+                    if r.next_task >= r.end_task:
+                        r.count, r.finish = r.acc, now
+                        r.done.set()
+                    elif self.max_slices is not None and r.slices >= self.max_slices:
+                        r.error = TimeoutError(f"request {r.rid} exceeded {self.max_slices} slices")
+                        r.finish = now
+                        r.done.set()
+                    else:
+                        still.append(r)
+                self._active = still
+
+
+def poisson_arrivals(rate, count, seed):
+    """Arrival offsets (seconds) of a Poisson process, from the project PRNG."""
+    from synth.rng import stream, uniform01
+    u = uniform01(stream(seed, 0, count))
+    return np.cumsum(-np.log1p(-u) / rate)
