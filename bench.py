@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--patterns", default=None, help="comma list overriding the workload's patterns")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU-baseline sample budget")
+    ap.add_argument("--batched-graph", default="rmat12",
+                    help="graph of the batched comparison ('' to skip)")
     return ap.parse_args()
 
 
@@ -319,6 +321,10 @@ def gpu_arm(a, rank, world):
         e2e_ms.append((time.time() - t) * 1000.0)
         del g2
 
+    batched = None
+    if a.batched_graph and world == 1:
+        batched = batched_compare(N, stream, a.batched_graph)
+
     hbm, peak_kind = peaks()
     mean_kern = {p: statistics.mean(v) for p, v in kern_ms.items()}
     kern_total_ms = sum(mean_kern.values())
@@ -369,8 +375,45 @@ def gpu_arm(a, rank, world):
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
         },
         "clocks": clk,
+        "batched": batched,
     }
     return out, (n, src, dst, pats)
+
+
+def batched_compare(N, stream, graph_name, npat=64, top_k=3, seed=64, reps=3):
+    """64 random connected 3-6-vertex patterns (edge probability 0.5), each
+    under its top-3 plans: one persistent launch for all jobs against one
+    launch per (pattern, plan) and against one launch per pattern (best plan).
+    Results must agree job by job."""
+    import torch
+    from synth import random_pattern_set
+    n, src, dst = workload_edges(graph_name)
+    g = N.gp_graph_create_edges(src, dst, n, N.GP_DEGREE_ORDER, stream=stream)
+    pats = random_pattern_set(npat, 3, 6, 0.5, seed)
+    scheds = [N.gp_schedule(N.gp_pattern_create(adj), g, top_k=top_k, stream=stream) for adj in pats]
+    jobs = [(s, i) for s in scheds for i in range(len(s))]
+    G, S, I = [g] * len(jobs), [s for s, _ in jobs], [i for _, i in jobs]
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return r, e0.elapsed_time(e1) / 1000.0
+
+    batched, _ = timed(lambda: N.gp_count_batch(G, S, I, stream=stream))      # warm-up
+    single = [N.gp_count(g, s, i, stream=stream)[1] for s, i in jobs]
+    if [int(x) for x in batched] != single:
+        raise AssertionError("batched counts differ from single launches")
+    tb = min(timed(lambda: N.gp_count_batch(G, S, I, stream=stream))[1] for _ in range(reps))
+    ts = min(timed(lambda: [N.gp_count(g, s, i, stream=stream) for s, i in jobs])[1] for _ in range(reps))
+    tp = min(timed(lambda: [N.gp_count(g, s, 0, stream=stream) for s in scheds])[1] for _ in range(reps))
+    return {"graph": graph_name, "patterns": npat, "jobs": len(jobs), "batched_s": tb,
+            "per_plan_launches_s": ts, "per_pattern_launches_s": tp,
+            "speedup_vs_per_plan": ts / tb, "speedup_vs_per_pattern": tp / tb,
+            "counts_agree": True}
 
 
 def reference_arm(a):

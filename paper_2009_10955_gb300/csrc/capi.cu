@@ -85,6 +85,7 @@ gp_status triangle_count(gp_graph* g, cudaStream_t st, uint64_t* out) {
     job.task_begin = 0;
     job.ntasks = g->nnz;
     job.task_offset = 0;
+    job.heavy = g->heavy_end;
     uint64_t res2[2] = {0, 0};
     int64_t done = 0;
     gp_status rc = run_count(&job, 1, LaunchOpts(), st, res2, &done);
@@ -113,6 +114,7 @@ gp_status make_job(gp_graph* g, const gp_schedules* s, int32_t idx, const gp_cou
     }
     job->task_begin = b;
     job->ntasks = e - b;
+    job->heavy = std::min<int64_t>(std::max<int64_t>(g->heavy_end - b, 0), e - b);
     return GP_OK;
 }
 

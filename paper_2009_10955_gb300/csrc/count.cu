@@ -417,11 +417,26 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
     const long long t_start = clock64();
     for (;;) {
         if (budget > 0 && clock64() - t_start > budget) break;
+        // Grab one task while the cursor is inside some job's heavy prefix
+        // (tasks of high-degree first vertices), a chunk otherwise.
         unsigned long long t0 = 0;
-        if (lane == 0) t0 = atomicAdd(cursor, (unsigned long long)chunk);
+        int grab = chunk;
+        if (lane == 0) {
+            const int64_t peek = (int64_t)*(volatile unsigned long long*)cursor;
+            if (peek < total) {
+                int lo = 0, hi = njobs - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (jobs[mid].task_offset <= peek) lo = mid; else hi = mid - 1;
+                }
+                if (peek - jobs[lo].task_offset < jobs[lo].heavy) grab = 1;
+            }
+            t0 = atomicAdd(cursor, (unsigned long long)grab);
+        }
         t0 = __shfl_sync(kFull, t0, 0);
+        grab = __shfl_sync(kFull, grab, 0);
         if ((int64_t)t0 >= total) break;
-        const int64_t t1 = min((int64_t)t0 + chunk, total);
+        const int64_t t1 = min((int64_t)t0 + grab, total);
         int64_t t = (int64_t)t0;
         while (t < t1) {
             if (cur_job < 0 || t < job_lo || t >= job_hi) {
@@ -540,8 +555,10 @@ gp_status geometry(const CountJob* jobs, int njobs, const LaunchOpts& opt, Geome
     GP_CUDA_TRY(cudaGetDevice(&dev));
     GP_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     int occ = 0;
-    // two register budgets: about 96 registers (2 blocks per SM) or 64 (4)
-    const bool dense = opt.blocks_per_sm >= 3;
+    // two register budgets: 64 registers (4 blocks per SM, the default: the
+    // kernel is latency-bound and gains more from warps than from registers)
+    // or about 96 (2 blocks per SM, when 1 or 2 blocks per SM are asked for)
+    const bool dense = !(opt.blocks_per_sm == 1 || opt.blocks_per_sm == 2);
     g->kern = opt.stats ? (dense ? k_count<true, 4> : k_count<true, 1>)
                         : (dense ? k_count<false, 4> : k_count<false, 1>);
     GP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, g->kern, kWarps * 32, 0));

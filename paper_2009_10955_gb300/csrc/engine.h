@@ -17,6 +17,8 @@ struct gp_graph {
     int32_t n = 0;
     int64_t nnz = 0;              // directed entries = 2 |E|
     int32_t max_deg = 0;
+    int64_t heavy_end = 0;        // CSR entries of the leading vertices of degree
+                                  // >= kHeavyDegree (degree-ordered graphs only)
     int64_t* row_ptr = nullptr;   // device, n + 1
     int32_t* col = nullptr;       // device, nnz
     int32_t* perm = nullptr;      // device, n (new id -> input id) or null
@@ -38,6 +40,10 @@ gp_status csr_to_pairs(const int64_t* d_row_ptr, const int32_t* d_col, int32_t n
                        int32_t* d_src, int32_t* d_dst, cudaStream_t st);
 // Maximum degree of a device CSR (graph.cu).
 gp_status max_degree(const int64_t* d_row_ptr, int32_t n, cudaStream_t st, int32_t* out);
+// First CSR entry of the first vertex whose degree is below min_deg, for a
+// graph whose degrees do not increase with the id (graph.cu).
+gp_status heavy_prefix(const int64_t* d_row_ptr, int32_t n, int32_t min_deg, cudaStream_t st,
+                       int64_t* out);
 
 // One counting job for the device (count.cu).
 struct CountJob {
@@ -49,7 +55,12 @@ struct CountJob {
     int64_t task_begin;      // first CSR entry (edge task) of this job
     int64_t ntasks;          // edge tasks of this job
     int64_t task_offset;     // first global task index of this job
+    int64_t heavy;           // leading tasks of this job handed out one at a time
 };
+
+// Vertices of at least this degree start tasks heavy enough to be handed out
+// one per grab (degree-ordered graphs put them first).
+constexpr int32_t kHeavyDegree = 256;
 
 struct LaunchOpts {
     int warps_per_block = 8;

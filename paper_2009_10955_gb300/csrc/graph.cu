@@ -167,7 +167,32 @@ gp_status keys_to_csr(const uint64_t* d_keys, int64_t nnz, int32_t n, cudaStream
     return GP_OK;
 }
 
+// One thread: binary search for the first vertex of degree < min_deg.
+__global__ void k_heavy_prefix(const int64_t* __restrict__ row_ptr, int32_t n, int32_t min_deg,
+                               int64_t* __restrict__ out) {
+    int32_t lo = 0, hi = n;
+    while (lo < hi) {
+        int32_t mid = lo + ((hi - lo) >> 1);
+        if (row_ptr[mid + 1] - row_ptr[mid] >= min_deg) lo = mid + 1; else hi = mid;
+    }
+    *out = row_ptr[lo];
+}
+
 }  // namespace
+
+gp_status heavy_prefix(const int64_t* d_row_ptr, int32_t n, int32_t min_deg, cudaStream_t st,
+                       int64_t* out) {
+    Scratch s(st);
+    GP_CUDA_TRY(s.alloc(sizeof(int64_t)));
+    k_heavy_prefix<<<1, 1, 0, st>>>(d_row_ptr, n, min_deg, s.as<int64_t>());
+    count_launch();
+    GP_CUDA_TRY(cudaGetLastError());
+    int64_t h = 0;
+    GP_CUDA_TRY(cudaMemcpyAsync(&h, s.p, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    GP_CUDA_TRY(cudaStreamSynchronize(st));
+    *out = h;
+    return GP_OK;
+}
 
 gp_status max_degree(const int64_t* d_row_ptr, int32_t n, cudaStream_t st, int32_t* out) {
     Scratch s(st);
@@ -294,8 +319,7 @@ gp_status build_graph(const int32_t* d_src, const int32_t* d_dst, int64_t m, int
     rc = keys_to_csr(keys_a.as<uint64_t>(), nnz, n, st, g);
     if (rc != GP_OK) { cudaFree(new2old); return rc; }
     g->perm = new2old;
-    GP_CUDA_TRY(cudaStreamSynchronize(st));
-    return GP_OK;
+    return heavy_prefix(g->row_ptr, n, kHeavyDegree, st, &g->heavy_end);
 }
 
 }  // namespace gp
