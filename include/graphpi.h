@@ -238,6 +238,25 @@ gp_status gp_count_batch_ranges(gp_graph* const* graphs, const gp_schedules* con
 gp_status gp_count_scratch_bytes(const gp_graph* g, const gp_schedules* s, int32_t idx,
                                  const gp_count_opts* opts, uint64_t* bytes);
 
+/* gp_count without any memory allocation, for callers that cannot allocate
+ * device memory when they count (an arena or pool owns the device memory,
+ * a host application forbids cudaMalloc/cudaFree on its streams, or the
+ * allocation's latency is unacceptable). The paper has no counterpart: it
+ * is an interface choice of this library. Results, job table and
+ * intermediate sets go into one fixed 64 MiB device array that the library
+ * holds on every GPU it is loaded on until the process exits; the launch
+ * uses as many blocks as fit there, so it can be much slower than gp_count.
+ * A plan and graph needing more than the array holds per block of 8 warps
+ * (8 x intermediate sets x max degree x 4 bytes) fail with GP_ERR_SCRATCH.
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture. All calls share
+ * the array and it keeps the last call's contents (each call clears what
+ * must start at zero): calls that overlap on the GPU, from any thread or
+ * stream, race and must be serialised by the caller. Counts all edge tasks;
+ * writes *out on GP_OK; synchronises `stream`. */
+gp_status gp_count_noalloc(gp_graph* g, const gp_schedules* s, int32_t idx, void* stream,
+                           uint64_t* out);
+
 /* ------------------------------------------------------------------ misc */
 
 const char* gp_status_str(gp_status s);

@@ -54,6 +54,7 @@ SIGNATURES = {
     "gp_count_batch": (i32, [P, P, P, i32, P, P, P]),
     "gp_count_batch_ranges": (i32, [P, P, P, P, P, i32, P, P, P, P]),
     "gp_count_scratch_bytes": (i32, [P, P, i32, P, P]),
+    "gp_count_noalloc": (i32, [P, P, i32, P, P]),
     "gp_status_str": (ctypes.c_char_p, [i32]),
     "gp_last_error": (ctypes.c_char_p, []),
     "gp_take_launch_count": (i64, []),
@@ -240,6 +241,14 @@ def gp_config_cost(pattern, order, restrictions, n_vertices, n_edges, tri_cnt):
     check(lib().gp_config_cost(pattern.h, _ptr(order), _ptr(res) if res.size else None, res.shape[0],
                                float(n_vertices), float(n_edges), float(tri_cnt), ctypes.byref(out)),
           "gp_config_cost")
+    return out.value
+
+
+def gp_count_noalloc(graph, schedules, idx=0, stream=None):
+    """Count with the library's fixed device scratch (no allocation)."""
+    out = ctypes.c_uint64()
+    check(lib().gp_count_noalloc(graph.h, schedules.h, idx, _stream(stream), ctypes.byref(out)),
+          "gp_count_noalloc")
     return out.value
 
 

@@ -134,6 +134,13 @@ bool opts_ok(const gp_count_opts* o) {
 }
 
 }  // namespace
+
+gp_status single_job(gp_graph* g, const gp_schedules* s, int32_t idx, CountJob* job) {
+    gp_status rc = make_job(g, s, idx, nullptr, job);
+    if (rc != GP_OK) return rc;
+    return ensure_device(g);
+}
+
 }  // namespace gp
 
 using namespace gp;

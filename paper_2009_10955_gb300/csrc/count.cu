@@ -663,4 +663,64 @@ gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& opt, cuda
     return rc;
 }
 
+gp_status run_count_in_scratch(const CountJob* jobs, int njobs, void* d_scratch, size_t scratch_bytes,
+                               cudaStream_t st, uint64_t* results) {
+    constexpr int kMaxJobs = 8;            // host result words live on the stack
+    if (njobs <= 0 || njobs > kMaxJobs) { set_error("1 to %d jobs per call", kMaxJobs); return GP_ERR_ARG; }
+    // layout: [result words | job table | intermediate sets], 256-byte aligned
+    const size_t words_b = ((sizeof(unsigned long long) * (2 * (size_t)njobs + 3)) + 255) & ~(size_t)255;
+    const size_t jobs_b = ((sizeof(CountJob) * (size_t)njobs) + 255) & ~(size_t)255;
+    if (words_b + jobs_b > scratch_bytes) {
+        set_error("%d jobs need %zu bytes of fixed scratch for results and job table; it holds %zu",
+                  njobs, words_b + jobs_b, scratch_bytes);
+        return GP_ERR_SCRATCH;
+    }
+    int64_t total = 0, warp_elems = 1;
+    for (int j = 0; j < njobs; ++j) {
+        total += jobs[j].ntasks;
+        warp_elems = std::max<int64_t>(warp_elems, (int64_t)jobs[j].plan.nslots * jobs[j].slot_cap);
+    }
+    const size_t per_block = (size_t)kWarps * (size_t)warp_elems * sizeof(int32_t);
+    const size_t slot_b = scratch_bytes - words_b - jobs_b;
+    if (per_block > slot_b) {
+        set_error("this plan and graph need %zu bytes of intermediate-set scratch per block; "
+                  "the fixed scratch has %zu", per_block, slot_b);
+        return GP_ERR_SCRATCH;
+    }
+    int dev = 0, nsm = 0, occ = 0;
+    GP_CUDA_TRY(cudaGetDevice(&dev));
+    GP_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    auto kern = k_count<false, 4>;
+    GP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWarps * 32, 0));
+    int64_t blocks = std::min<int64_t>((int64_t)nsm * std::max(occ, 1), (int64_t)(slot_b / per_block));
+    int64_t per_warp = total / (blocks * kWarps * 64);
+    const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(64, per_warp));
+    char* base = static_cast<char*>(d_scratch);
+    unsigned long long* d_res = reinterpret_cast<unsigned long long*>(base);
+    unsigned long long* d_cursor = d_res + 2 * njobs;
+    int* d_err = reinterpret_cast<int*>(d_cursor + 1);
+    unsigned long long* d_stats = d_cursor + 2;
+    CountJob* d_jobs = reinterpret_cast<CountJob*>(base + words_b);
+    int32_t* d_slots = reinterpret_cast<int32_t*>(base + words_b + jobs_b);
+    unsigned long long h_res[2 * kMaxJobs + 3] = {};
+    const size_t nwords = 2 * (size_t)njobs + 3;
+    GP_CUDA_TRY(cudaMemcpyAsync(d_jobs, jobs, sizeof(CountJob) * (size_t)njobs, cudaMemcpyHostToDevice, st));
+    GP_CUDA_TRY(cudaMemsetAsync(d_res, 0, words_b, st));       // results, cursor, error word start at 0
+    if (total > 0) {
+        kern<<<(unsigned)blocks, kWarps * 32, 0, st>>>(d_jobs, njobs, total, d_cursor, d_res, d_slots,
+                                                      warp_elems, chunk, 0, d_err, d_stats);
+        count_launch();
+        GP_CUDA_TRY(cudaGetLastError());
+    }
+    GP_CUDA_TRY(cudaMemcpyAsync(h_res, d_res, sizeof(unsigned long long) * nwords,
+                                cudaMemcpyDeviceToHost, st));
+    GP_CUDA_TRY(cudaStreamSynchronize(st));
+    if ((int)(h_res[2 * njobs + 1] & 0xffffffffu)) {
+        set_error("count kernel reported internal error %d", (int)(h_res[2 * njobs + 1] & 0xffffffffu));
+        return GP_ERR_INTERNAL;
+    }
+    for (int j = 0; j < 2 * njobs; ++j) results[j] = h_res[j];
+    return GP_OK;
+}
+
 }  // namespace gp

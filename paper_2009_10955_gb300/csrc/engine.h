@@ -80,6 +80,17 @@ gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& lo, cudaS
 // Device scratch run_count would allocate for these jobs and options.
 gp_status scratch_bytes(const CountJob* jobs, int njobs, const LaunchOpts& lo, uint64_t* bytes);
 
+// run_count without allocating: results, job table and intermediate sets all
+// live in the caller's device buffer d_scratch (256-byte aligned); the grid
+// shrinks to what that buffer holds. GP_ERR_SCRATCH when not even one block
+// fits.
+gp_status run_count_in_scratch(const CountJob* jobs, int njobs, void* d_scratch, size_t scratch_bytes,
+                               cudaStream_t st, uint64_t* results);
+
+// The job of plan idx of s over all edge tasks of g, with g's device made
+// current (capi.cu).
+gp_status single_job(gp_graph* g, const gp_schedules* s, int32_t idx, CountJob* job);
+
 }  // namespace gp
 
 #define GP_CUDA_TRY(expr)                                                          \
