@@ -55,8 +55,15 @@ def parse():
     ap.add_argument("--patterns", default=None, help="comma list overriding the workload's patterns")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU-baseline sample budget")
-    ap.add_argument("--batched-graph", default="rmat12",
-                    help="graph of the batched comparison ('' to skip)")
+    ap.add_argument("--batched-graphs", default="rmat12,rmat11,rmat10,rmat9,rmat8",
+                    help="candidate graphs of the batched comparison, largest first ('' to skip)")
+    ap.add_argument("--mode", default="count", choices=["count", "serve"],
+                    help="serve: the continuous-batching sweep instead of the count benchmark")
+    ap.add_argument("--serve-scales", default="14,15,16,17,18,19,20,22")
+    ap.add_argument("--serve-rates", default="10,30,100,300,1000")
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-deadline", type=float, default=2.0)
+    ap.add_argument("--serve-slice-ms", type=float, default=5.0)
     return ap.parse_args()
 
 
@@ -322,8 +329,8 @@ def gpu_arm(a, rank, world):
         del g2
 
     batched = None
-    if a.batched_graph and world == 1:
-        batched = batched_compare(N, stream, a.batched_graph)
+    if a.batched_graphs and world == 1:
+        batched = batched_compare(N, stream, a.batched_graphs.split(","))
 
     hbm, peak_kind = peaks()
     mean_kern = {p: statistics.mean(v) for p, v in kern_ms.items()}
@@ -380,18 +387,38 @@ def gpu_arm(a, rank, world):
     return out, (n, src, dst, pats)
 
 
-def batched_compare(N, stream, graph_name, npat=64, top_k=3, seed=64, reps=3):
+def batched_compare(N, stream, graph_names, npat=64, top_k=3, seed=64, reps=3, budget_s=2.0):
     """64 random connected 3-6-vertex patterns (edge probability 0.5), each
     under its top-3 plans: one persistent launch for all jobs against one
     launch per (pattern, plan) and against one launch per pattern (best plan).
-    Results must agree job by job."""
+    Results must agree job by job. The first graph of `graph_names` on which
+    every job finishes within `budget_s` of device time (checked with one
+    budgeted time slice) is used; larger R-MAT graphs hold tree patterns
+    whose enumeration takes hours."""
     import torch
     from synth import random_pattern_set
-    n, src, dst = workload_edges(graph_name)
-    g = N.gp_graph_create_edges(src, dst, n, N.GP_DEGREE_ORDER, stream=stream)
     pats = random_pattern_set(npat, 3, 6, 0.5, seed)
-    scheds = [N.gp_schedule(N.gp_pattern_create(adj), g, top_k=top_k, stream=stream) for adj in pats]
-    jobs = [(s, i) for s in scheds for i in range(len(s))]
+    chosen, skipped = None, []
+    for graph_name in graph_names:
+        n, src, dst = workload_edges(graph_name)
+        g = N.gp_graph_create_edges(src, dst, n, N.GP_DEGREE_ORDER, stream=stream)
+        scheds = [N.gp_schedule(N.gp_pattern_create(adj), g, top_k=top_k, stream=stream) for adj in pats]
+        jobs = [(s, i) for s in scheds for i in range(len(s))]
+        nnz = g.device_csr()[2]
+        try:
+            st, _, _ = N.gp_count_batch_ranges([g] * len(jobs), [s for s, _ in jobs], [i for _, i in jobs],
+                                               [0] * len(jobs), [nnz] * len(jobs),
+                                               N.make_opts(budget_cycles=int(budget_s * 1.9e9)), stream=stream)
+        except N.GraphPiError as e:        # e.g. a count beyond 64 bits
+            skipped.append(f"{graph_name}: {e.status}")
+            continue
+        if st == N.GP_OK:
+            chosen = graph_name
+            break
+        skipped.append(f"{graph_name}: not done in {budget_s} s")
+    if chosen is None:
+        return {"skipped": skipped}
+    graph_name = chosen
     G, S, I = [g] * len(jobs), [s for s, _ in jobs], [i for _, i in jobs]
 
     def timed(fn):
@@ -410,10 +437,53 @@ def batched_compare(N, stream, graph_name, npat=64, top_k=3, seed=64, reps=3):
     tb = min(timed(lambda: N.gp_count_batch(G, S, I, stream=stream))[1] for _ in range(reps))
     ts = min(timed(lambda: [N.gp_count(g, s, i, stream=stream) for s, i in jobs])[1] for _ in range(reps))
     tp = min(timed(lambda: [N.gp_count(g, s, 0, stream=stream) for s in scheds])[1] for _ in range(reps))
-    return {"graph": graph_name, "patterns": npat, "jobs": len(jobs), "batched_s": tb,
+    return {"graph": graph_name, "skipped_graphs": skipped, "patterns": npat, "jobs": len(jobs), "batched_s": tb,
             "per_plan_launches_s": ts, "per_pattern_launches_s": tp,
             "speedup_vs_per_plan": ts / tb, "speedup_vs_per_pattern": tp / tb,
             "counts_agree": True}
+
+
+def serve_bench(N, stream, scales, rates, per_rate, deadline_s, slice_ms, seed=777):
+    """Continuous-batching server over several device-resident R-MAT graphs
+    (scale s, edge factor 16, seed 100 + s) under Poisson arrivals of random
+    connected 3-6-vertex patterns (edge probability 0.5). Requests that need
+    more than `deadline_s` of service are answered with a timeout."""
+    from synth import random_pattern_set
+    from synth.graphs import rmat_edges
+    from paper_2009_10955_gb300.serve import Server, poisson_arrivals
+    graphs = {}
+    for sc in scales:
+        src, dst = rmat_edges(sc, 16, 0.57, 0.19, 0.19, seed=100 + sc)
+        graphs[f"rmat{sc}"] = N.gp_graph_create_edges(src, dst, 1 << sc, N.GP_DEGREE_ORDER, stream=stream)
+    names = sorted(graphs)
+    pats = random_pattern_set(64, 3, 6, 0.5, seed)
+    rows = []
+    for ri, rate in enumerate(rates):
+        arr = poisson_arrivals(rate, per_rate, seed + ri)
+        srv = Server(graphs, slice_ms=slice_ms, stream=stream,
+                     max_slices=max(1, int(deadline_s * 1000.0 / slice_ms)))
+        t0 = time.perf_counter()
+        reqs = []
+        for i, at in enumerate(arr):
+            delay = t0 + at - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            reqs.append(srv.submit(names[i % len(names)], pats[i % len(pats)]))
+        for r in reqs:
+            r.done.wait(3600)
+        srv.close()
+        ok = [r for r in reqs if r.error is None]
+        lat = sorted(r.latency for r in ok)
+        span = max(r.finish for r in reqs) - t0
+        rows.append({"rate": rate, "requests": len(reqs), "completed": len(ok),
+                     "timeouts": sum(isinstance(r.error, TimeoutError) for r in reqs),
+                     "errors": sum(r.error is not None and not isinstance(r.error, TimeoutError) for r in reqs),
+                     "p50_s": lat[len(lat) // 2] if lat else None,
+                     "p99_s": lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None,
+                     "counts_per_s": len(ok) / span if span > 0 else None,
+                     "slices": srv.slices})
+    return {"metric": "serving latency and throughput", "graphs": names, "slice_ms": slice_ms,
+            "deadline_s": deadline_s, "rows": rows}
 
 
 def reference_arm(a):
@@ -447,6 +517,15 @@ def main():
             print(json.dumps(reference_arm(a)), flush=True)
         return
     import torch
+    if a.mode == "serve":
+        if rank == 0:
+            from paper_2009_10955_gb300 import native
+            N = native()
+            out = serve_bench(N, torch.cuda.current_stream(), [int(x) for x in a.serve_scales.split(",")],
+                              [float(x) for x in a.serve_rates.split(",")], a.serve_requests,
+                              a.serve_deadline, a.serve_slice_ms)
+            print(json.dumps(out), flush=True)
+        return
     if world > 1:
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))

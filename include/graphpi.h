@@ -157,6 +157,19 @@ gp_status gp_schedule(const gp_pattern* p, gp_graph* g, int32_t top_k, void* str
 gp_status gp_schedule_explicit(const gp_pattern* p, const int32_t* order, const int32_t* restr,
                                int32_t n_restr, gp_schedules** out);
 
+/* Switch the plans of s to (enable != 0) or from inclusion-exclusion
+ * counting of the last two loops (Section IV-D with k = 2). A plan qualifies
+ * when k >= 4 and its last two searched vertices are not adjacent; the
+ * restrictions acting at those two loops are dropped and the total is
+ * divided by the number of automorphic copies of each embedding that the
+ * remaining restrictions still admit. The paper computes that number with
+ * no_conflict; here it is counted exactly over all k! relative vertex
+ * orders and the plan keeps plain enumeration when it is not the same for
+ * every order. *n_iep (may be NULL) receives how many plans switched.
+ * Inclusion-exclusion plans count whole graphs only: gp_count with a task
+ * range or budget, and gp_count_batch_ranges, reject them with GP_ERR_ARG. */
+gp_status gp_schedule_set_iep(gp_schedules* s, int32_t enable, int32_t* n_iep);
+
 /* Number of plans held. */
 gp_status gp_schedule_size(const gp_schedules* s, int32_t* count);
 
@@ -194,14 +207,20 @@ typedef struct gp_count_opts {
                                  kernel, from CUDA events recorded around its launch
                                  on the caller's stream                               */
     uint64_t* algo_bytes;     /* host out (with GP_COUNT_STATS): algorithmic bytes of
-                                 the count -- 4 bytes per element of every clipped
-                                 intersection operand, per stored intersection
-                                 result and per iterated candidate                   */
+                                 the count -- per intersection the cheaper of a merge
+                                 (4 bytes per clipped operand element) and a binary
+                                 search counted in 32-byte sectors, plus 4 bytes per
+                                 stored result element and per iterated candidate    */
+    int32_t lane_work;        /* probe/merge steps above which a lane hands its
+                                 last-level count to the whole warp (0 = 192)        */
+    int32_t reserved1;
 } gp_count_opts;
 
 /* gp_count_opts.flags */
 #define GP_COUNT_STATS 1   /* run the instrumented kernel that tallies algo_bytes
                               (slower; for measurement only)                      */
+#define GP_COUNT_NO_CORE 2 /* never use the core adjacency bit matrix: every
+                              membership test is a binary search                  */
 
 /* Count the embeddings of the pattern of `s` in `g` with plan `idx`.
  * Every embedding is counted exactly once (restrictions, Algorithm 1).

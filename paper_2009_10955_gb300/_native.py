@@ -28,6 +28,7 @@ GP_DEVICE_PTRS = 1
 GP_DEGREE_ORDER = 2
 GP_ASSUME_CLEAN = 4
 GP_COUNT_STATS = 1
+GP_COUNT_NO_CORE = 2
 
 # Every function the header declares, with its ctypes signature.
 P = ctypes.c_void_p
@@ -47,6 +48,7 @@ SIGNATURES = {
     "gp_schedule": (i32, [P, P, i32, P, P]),
     "gp_schedule_explicit": (i32, [P, P, P, i32, P]),
     "gp_schedule_size": (i32, [P, P]),
+    "gp_schedule_set_iep": (i32, [P, i32, P]),
     "gp_schedule_get": (i32, [P, i32, P, P, P, P]),
     "gp_config_cost": (i32, [P, P, P, i32, f64, f64, f64, P]),
     "gp_schedule_destroy": (None, [P]),
@@ -75,6 +77,8 @@ class gp_count_opts(ctypes.Structure):
         ("resume_cursor", ctypes.POINTER(ctypes.c_int64)),
         ("kernel_ms", ctypes.POINTER(ctypes.c_float)),
         ("algo_bytes", ctypes.POINTER(ctypes.c_uint64)),
+        ("lane_work", ctypes.c_int32),
+        ("reserved1", ctypes.c_int32),
     ]
 
 
@@ -339,6 +343,11 @@ class Schedules:
         if getattr(self, "h", None) and _lib is not None:
             _lib.gp_schedule_destroy(self.h)
             self.h = None
+
+    def set_iep(self, enable=True):
+        n = ctypes.c_int32()
+        check(lib().gp_schedule_set_iep(self.h, 1 if enable else 0, ctypes.byref(n)), "gp_schedule_set_iep")
+        return n.value
 
     def __len__(self):
         c = ctypes.c_int32()

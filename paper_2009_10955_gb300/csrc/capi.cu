@@ -19,6 +19,7 @@ struct gp_schedules {
     int k = 0;
     std::vector<gp::Config> configs;
     std::vector<GpPlan> plans;
+    std::unique_ptr<gp::PatternInfo> info;   // for recompiling (inclusion-exclusion)
 };
 
 namespace gp {
@@ -57,6 +58,7 @@ void free_graph(gp_graph* g) {
     if (g->row_ptr) cudaFree(g->row_ptr);
     if (g->col) cudaFree(g->col);
     if (g->perm) cudaFree(g->perm);
+    if (g->core_bits) cudaFree(g->core_bits);
     delete g;
 }
 
@@ -85,7 +87,10 @@ gp_status triangle_count(gp_graph* g, cudaStream_t st, uint64_t* out) {
     job.task_begin = 0;
     job.ntasks = g->nnz;
     job.task_offset = 0;
-    job.heavy = g->heavy_end;
+    job.heavy = 0;                              // three-vertex plan: full chunks
+    job.core_bits = g->core_bits;
+    job.core_n = g->core_n;
+    job.core_words = g->core_words;
     uint64_t res2[2] = {0, 0};
     int64_t done = 0;
     gp_status rc = run_count(&job, 1, LaunchOpts(), st, res2, &done);
@@ -114,8 +119,38 @@ gp_status make_job(gp_graph* g, const gp_schedules* s, int32_t idx, const gp_cou
     }
     job->task_begin = b;
     job->ntasks = e - b;
-    job->heavy = std::min<int64_t>(std::max<int64_t>(g->heavy_end - b, 0), e - b);
+    // single-task grabs only pay off where a task runs loops of its own; a
+    // three-vertex plan handles one task per lane and wants full chunks
+    job->heavy = job->plan.k == 3 ? 0 : std::min<int64_t>(std::max<int64_t>(g->heavy_end - b, 0), e - b);
+    job->core_bits = g->core_bits;
+    job->core_n = g->core_n;
+    job->core_words = g->core_words;
     return GP_OK;
+}
+
+// A job's count from its 128-bit device total: inclusion-exclusion plans
+// divide by their multiplicity, exactly.
+gp_status finish_total(const GpPlan& plan, uint64_t lo, uint64_t hi, uint64_t* out) {
+    unsigned __int128 t = ((unsigned __int128)hi << 64) | lo;
+    if (plan.iep) {
+        const unsigned __int128 d = plan.iep_div ? plan.iep_div : 1;
+        if (t % d) return fail(GP_ERR_INTERNAL, "inclusion-exclusion total is not a multiple of its divisor");
+        t /= d;
+    }
+    if (t >> 64) return fail(GP_ERR_OVERFLOW, "count does not fit in 64 bits");
+    *out = (uint64_t)t;
+    return GP_OK;
+}
+
+std::unique_ptr<PatternInfo> clone_pattern(const PatternInfo& p) {
+    std::unique_ptr<PatternInfo> q(new (std::nothrow) PatternInfo());
+    if (!q) return q;
+    uint8_t adj[GP_MAX_K * GP_MAX_K];
+    for (int a = 0; a < p.k; ++a)
+        for (int b = 0; b < p.k; ++b) adj[a * p.k + b] = p.adj[a][b];
+    std::string err;
+    if (!pattern_init(*q, adj, p.k, err)) q.reset();
+    return q;
 }
 
 LaunchOpts launch_opts(const gp_count_opts* o) {
@@ -125,6 +160,8 @@ LaunchOpts launch_opts(const gp_count_opts* o) {
         if (o->chunk > 0) lo.chunk = o->chunk;
         if (o->budget_cycles > 0) lo.budget_cycles = o->budget_cycles;
         lo.stats = (o->flags & GP_COUNT_STATS) != 0;
+        lo.no_core = (o->flags & GP_COUNT_NO_CORE) != 0;
+        if (o->lane_work > 0) lo.lane_work = o->lane_work;
     }
     return lo;
 }
@@ -139,6 +176,10 @@ gp_status single_job(gp_graph* g, const gp_schedules* s, int32_t idx, CountJob* 
     gp_status rc = make_job(g, s, idx, nullptr, job);
     if (rc != GP_OK) return rc;
     return ensure_device(g);
+}
+
+gp_status job_total(const CountJob& job, const uint64_t* res, uint64_t* out) {
+    return finish_total(job.plan, res[0], res[1], out);
 }
 
 }  // namespace gp
@@ -368,6 +409,8 @@ gp_status gp_schedule(const gp_pattern* p, gp_graph* g, int32_t top_k, void* str
     if (!s) return fail(GP_ERR_NOMEM, "host allocation failed");
     gp_pattern* pm = const_cast<gp_pattern*>(p);
     s->k = p->info.k;
+    s->info = clone_pattern(p->info);
+    if (!s->info) return fail(GP_ERR_NOMEM, "host allocation failed");
     s->configs = rank_configs(pm->info, V, E, T, top_k);
     if (s->configs.empty()) return fail(GP_ERR_PATTERN, "no configuration for this pattern");
     for (const Config& c : s->configs) {
@@ -402,6 +445,8 @@ gp_status gp_schedule_explicit(const gp_pattern* p, const int32_t* order, const 
     std::unique_ptr<gp_schedules> s(new (std::nothrow) gp_schedules());
     if (!s) return fail(GP_ERR_NOMEM, "host allocation failed");
     s->k = k;
+    s->info = clone_pattern(p->info);
+    if (!s->info) return fail(GP_ERR_NOMEM, "host allocation failed");
     s->configs.push_back({0.0, sched, res});
     s->plans.push_back(plan);
     *out = s.release();
@@ -462,6 +507,8 @@ gp_status gp_count(gp_graph* g, const gp_schedules* s, int32_t idx, const gp_cou
     CountJob job;
     gp_status rc = make_job(g, s, idx, opts, &job);
     if (rc != GP_OK) return rc;
+    if (job.plan.iep && (job.task_begin != 0 || job.ntasks != g->nnz || (opts && opts->budget_cycles > 0)))
+        return fail(GP_ERR_ARG, "inclusion-exclusion plans count whole graphs only (no task range or budget)");
     rc = ensure_device(g);
     if (rc != GP_OK) return rc;
     uint64_t res[2] = {0, 0};
@@ -472,16 +519,18 @@ gp_status gp_count(gp_graph* g, const gp_schedules* s, int32_t idx, const gp_cou
     rc = run_count(&job, 1, launch_opts(opts), static_cast<cudaStream_t>(stream), res, &done,
                    want_ms ? &ms : nullptr, &bytes);
     if (rc != GP_OK) return rc;
-    if (res[1]) return fail(GP_ERR_OVERFLOW, "count does not fit in 64 bits");
+    uint64_t total = 0;
+    rc = finish_total(job.plan, res[0], res[1], &total);
+    if (rc != GP_OK) return rc;
     if (want_ms) *opts->kernel_ms = ms;
     if (opts && opts->algo_bytes && (opts->flags & GP_COUNT_STATS)) *opts->algo_bytes = bytes;
     if (done < job.ntasks) {
         if (opts && opts->resume_cursor) *opts->resume_cursor = job.task_begin + done;
-        *out = res[0];
+        *out = total;
         return GP_PARTIAL;
     }
     if (opts && opts->resume_cursor) *opts->resume_cursor = job.task_begin + job.ntasks;
-    *out = res[0];
+    *out = total;
     return GP_OK;
 }
 
@@ -514,9 +563,12 @@ gp_status gp_count_batch(gp_graph* const* graphs, const gp_schedules* const* sch
     if (rc != GP_OK) return rc;
     if (want_ms) *opts->kernel_ms = ms;
     if (opts && opts->algo_bytes && (opts->flags & GP_COUNT_STATS)) *opts->algo_bytes = bytes;
-    for (int32_t j = 0; j < njobs; ++j)
-        if (res[2 * j + 1]) return fail(GP_ERR_OVERFLOW, "a count does not fit in 64 bits");
-    for (int32_t j = 0; j < njobs; ++j) out[j] = res[2 * j];
+    std::vector<uint64_t> tot((size_t)njobs);
+    for (int32_t j = 0; j < njobs; ++j) {
+        rc = finish_total(jobs[j].plan, res[2 * j], res[2 * j + 1], &tot[j]);
+        if (rc != GP_OK) return rc;
+    }
+    for (int32_t j = 0; j < njobs; ++j) out[j] = tot[j];
     return GP_OK;
 }
 
@@ -537,6 +589,7 @@ gp_status gp_count_batch_ranges(gp_graph* const* graphs, const gp_schedules* con
         r.task_end = task_end ? task_end[j] : 0;
         gp_status rc = make_job(graphs[j], scheds[j], idx ? idx[j] : 0, &r, &jobs[j]);
         if (rc != GP_OK) return rc;
+        if (jobs[j].plan.iep) return fail(GP_ERR_ARG, "inclusion-exclusion plans count whole graphs only");
         if (graphs[j]->device != graphs[0]->device) return fail(GP_ERR_ARG, "graphs on different devices");
         jobs[j].task_offset = off;
         off += jobs[j].ntasks;
@@ -561,6 +614,24 @@ gp_status gp_count_batch_ranges(gp_graph* const* graphs, const gp_schedules* con
     }
     if (want_ms) *opts->kernel_ms = ms;
     return all ? GP_OK : GP_PARTIAL;
+}
+
+gp_status gp_schedule_set_iep(gp_schedules* s, int32_t enable, int32_t* n_iep) {
+    if (!s || !s->info) return fail(GP_ERR_ARG, "null schedule");
+    std::vector<GpPlan> plans;
+    int32_t n = 0;
+    for (const Config& c : s->configs) {
+        GpPlan plan;
+        std::string err;
+        bool iep = enable && compile_plan_iep(*s->info, c.sched.data(), c.res, &plan, err);
+        if (!iep && !compile_plan(*s->info, c.sched.data(), c.res, &plan, err))
+            return fail(GP_ERR_INTERNAL, err.c_str());
+        n += iep;
+        plans.push_back(plan);
+    }
+    s->plans = plans;
+    if (n_iep) *n_iep = n;
+    return GP_OK;
 }
 
 gp_status gp_count_scratch_bytes(const gp_graph* g, const gp_schedules* s, int32_t idx,

@@ -4,18 +4,24 @@
 //
 // Work decomposition (Section IV-E, fine-grained tasks + work stealing):
 // every directed CSR entry (v0, v1) is one task that fixes the first two
-// loops. Tasks of all jobs form one global index space; a warp grabs a chunk
-// of consecutive tasks with one atomicAdd on a global cursor, so idle warps
-// take the next work immediately (the device analogue of stealing).
+// loops. Tasks of all jobs form one global index space; a warp grabs tasks
+// with one atomicAdd on a global cursor (one at a time while the cursor is in
+// the high-degree prefix of a job, a chunk otherwise), so idle warps take the
+// next work immediately (the device analogue of work stealing).
 //
 // Inside a task one warp runs the remaining loops depth-first. Candidate
 // sets are intersections of sorted neighbour lists, clipped to the window the
 // restrictions impose (a restriction becomes a bound on a sorted list, the
-// "break" of Section IV-B). Intersections are warp-cooperative: each lane
-// takes one element of the shorter list and binary-searches it in the longer
-// one, and ballot/popc compacts the matches. The innermost loop is never
-// enumerated: its contribution is the size of its clipped candidate set
-// minus the already-matched vertices inside it.
+// "break" of Section IV-B). An intersection iterates one list and tests each
+// element for membership in the other: with one bit probe when the other is
+// the neighbour list of a "core" vertex (the highest-degree vertices of a
+// degree-ordered graph, whose adjacency among themselves is kept as a bit
+// matrix), else with a binary search. Loops above the last two run one
+// candidate at a time with the whole warp cooperating on each intersection;
+// the loop at depth k-2 gives one candidate to each lane, which counts the
+// last level alone (heavy candidates go back to the whole warp). The last
+// loop is never enumerated: its contribution is the size of its clipped
+// candidate set minus the already-matched vertices inside it.
 //
 // Counts are accumulated per lane in 128 bits and reduced with warp shuffles;
 // one atomic pair (low word, carry into the high word) per warp per job
@@ -85,41 +91,31 @@ __device__ void flush(Acc& acc, unsigned long long* res) {
     acc.lo = acc.hi = 0;
 }
 
-// Warp-cooperative sorted intersection of A and B. Writes the (sorted)
-// result to out when out != nullptr and returns its size (warp-uniform).
-// With acc != nullptr each lane also adds its own matches to acc.
-__device__ __forceinline__ int warp_intersect(const int32_t* __restrict__ A, int na,
-                                              const int32_t* __restrict__ B, int nb,
-                                              int32_t* __restrict__ out, int cap, Acc* acc,
-                                              int lane, int* err, unsigned long long* sbytes) {
-    if (na > nb) {
-        const int32_t* t = A; A = B; B = t;
-        int tn = na; na = nb; nb = tn;
-    }
-    int total = 0, from = 0;
-    for (int base = 0; base < na; base += 32) {
-        int i = base + lane;
-        int x = 0, pos = nb;
-        bool f = false;
-        if (i < na) {
-            x = __ldg(A + i);
-            pos = from + lower_bound(B + from, nb - from, x);
-            f = pos < nb && __ldg(B + pos) == x;
-        }
-        unsigned m = __ballot_sync(kFull, f);
-        if (out && f) {
-            int at = total + __popc(m & lanemask_lt());
-            if (at < cap) out[at] = x; else atomicExch(err, 2);
-        }
-        if (acc && f) acc->add(1);
-        total += __popc(m);
-        int last = min(31, na - 1 - base);
-        from = __shfl_sync(kFull, pos, last);   // later elements are larger
-    }
-    if (sbytes && lane == 0)
-        *sbytes += intersect_bytes(na, nb) + (out ? 4ull * (unsigned long long)total : 0ull);
-    return total;
-}
+struct TaskCtx {
+    const GpPlan* P;
+    const int64_t* __restrict__ row_ptr;
+    const int32_t* __restrict__ col;
+    const uint32_t* __restrict__ core_bits;   // core_n x core_words adjacency bits
+    int core_n;
+    int core_words;
+    int32_t* slots;        // this warp's intermediate sets
+    int slot_cap;
+    int n_vertices;
+    int* slen;             // their lengths (shared memory, per warp)
+    uint32_t* bm;          // this warp's bitmap sets (shared memory) or null
+    int bm_stride;         // words per bitmap set
+    int lane;
+    int lane_work;         // per-lane work limit before handing to the warp
+    int* err;
+    unsigned long long* sbytes;   // algorithmic-byte tally (instrumented kernel only)
+};
+
+// A sorted list: [p, p + n). v >= 0 when it is (a window of) N(v).
+struct List {
+    const int32_t* p;
+    int n;
+    int v;
+};
 
 struct Window { int lo, hi; };   // candidates c with lo < c < hi
 
@@ -132,115 +128,152 @@ __device__ __forceinline__ Window window(uint8_t lo_mask, uint8_t hi_mask, const
     return w;
 }
 
-// Clip a sorted list to a window: returns [b, e).
-__device__ __forceinline__ void clip(const int32_t* a, int n, Window w, int& b, int& e) {
-    b = (w.lo < 0) ? 0 : lower_bound(a, n, w.lo + 1);
-    e = (w.hi == INT_MAX) ? n : lower_bound(a, n, w.hi);
+// Clip a sorted list to a window.
+__device__ __forceinline__ List clip(List a, Window w) {
+    int b = (w.lo < 0) ? 0 : lower_bound(a.p, a.n, w.lo + 1);
+    int e = (w.hi == INT_MAX) ? a.n : lower_bound(a.p, a.n, w.hi);
     if (e < b) e = b;
+    return List{a.p + b, e - b, a.v};
 }
 
-struct TaskCtx {
-    const GpPlan* P;
-    const int64_t* __restrict__ row_ptr;
-    const int32_t* __restrict__ col;
-    int32_t* slots;        // this warp's intermediate sets
-    int slot_cap;
-    int n_vertices;
-    int* slen;             // their lengths (shared memory, per warp)
-    int lane;
-    int* err;
-    unsigned long long* sbytes;   // algorithmic-byte tally (instrumented kernel only)
+__device__ __forceinline__ List nbr(const TaskCtx& c, int v) {
+    int64_t b = __ldg(c.row_ptr + v), e = __ldg(c.row_ptr + v + 1);
+    return List{c.col + b, (int)(e - b), v};
+}
+
+__device__ __forceinline__ List slot(const TaskCtx& c, int s) {
+    return List{c.slots + (size_t)s * c.slot_cap, c.slen[s], -1};
+}
+
+__device__ __forceinline__ bool is_core(const TaskCtx& c, int v) { return v >= 0 && v < c.core_n; }
+
+// Is x (< core_n) a neighbour of core vertex v?
+__device__ __forceinline__ bool core_bit(const TaskCtx& c, int v, int x) {
+    const uint32_t w = __ldg(c.core_bits + (size_t)v * c.core_words + (x >> 5));
+    return (w >> (x & 31)) & 1u;
+}
+
+// How an intersection runs: iterate `it` (clipped to the window) and test
+// each element against `pr`, by bit probe when pr is a core vertex's
+// neighbourhood (elements >= core_n are binary-searched in pr's tail), by
+// binary search otherwise.
+struct Probe {
+    List it;
+    List pr;        // by bitmap: full N(pr.v), searched from `tail`; else clipped
+    int tail;
+    bool bitmap;
 };
 
-__device__ __forceinline__ void nbr(const TaskCtx& c, int v, const int32_t*& p, int& n) {
-    int64_t b = __ldg(c.row_ptr + v), e = __ldg(c.row_ptr + v + 1);
-    p = c.col + b;
-    n = (int)(e - b);
-}
-
-__device__ __forceinline__ void run_builds(const TaskCtx& c, int d, const int* v) {
-    const GpLevel& L = c.P->lvl[d];
-    for (int q = 0; q < L.nbuild; ++q) {
-        const GpBuild& B = L.build[q];
-        const int32_t* a; int na;
-        if (B.base_kind == 1) nbr(c, v[B.base], a, na);
-        else { a = c.slots + (size_t)B.base * c.slot_cap; na = c.slen[B.base]; }
-        const int32_t* b; int nb;
-        nbr(c, v[d], b, nb);
-        Window w = window(B.lo_mask, B.hi_mask, v);
-        int a0, a1, b0, b1;
-        clip(a, na, w, a0, a1);
-        clip(b, nb, w, b0, b1);
-        int32_t* out = c.slots + (size_t)B.dst * c.slot_cap;
-        int n = warp_intersect(a + a0, a1 - a0, b + b0, b1 - b0, out, c.slot_cap, nullptr, c.lane, c.err,
-                               c.sbytes);
-        if (c.lane == 0) c.slen[B.dst] = n;
-        __syncwarp();
-    }
-}
-
-// Is x in the sorted list a[0, n)?
-__device__ __forceinline__ bool contains(const int32_t* a, int n, int x) {
-    int p = lower_bound(a, n, x);
-    return p < n && __ldg(a + p) == x;
-}
-
-// Contribution of the innermost loop given v[0..k-2].
-__device__ __forceinline__ void count_last(const TaskCtx& c, const int* v, Acc& acc) {
-    const GpPlan& P = *c.P;
-    const int L = P.k - 1;
-    const GpLevel& lv = P.lvl[L];
-    Window w = window(lv.lo_mask, lv.hi_mask, v);
-    if (P.last_count_only) {
-        const int32_t* a; int na;
-        if (P.last_base_kind == 1) nbr(c, v[P.last_base], a, na);
-        else { a = c.slots + (size_t)P.last_base * c.slot_cap; na = c.slen[P.last_base]; }
-        const int32_t* b; int nb;
-        nbr(c, v[L - 1], b, nb);
-        int a0, a1, b0, b1;
-        clip(a, na, w, a0, a1);
-        clip(b, nb, w, b0, b1);
-        warp_intersect(a + a0, a1 - a0, b + b0, b1 - b0, nullptr, 0, &acc, c.lane, c.err, c.sbytes);
-        // matched vertices inside the intersection are not new vertices
-        bool hit = false;
-        if (c.lane < L && (lv.excl_mask >> c.lane & 1)) {
-            int x = v[c.lane];
-            hit = x > w.lo && x < w.hi && contains(a + a0, a1 - a0, x) && contains(b + b0, b1 - b0, x);
+__device__ __forceinline__ Probe choose(const TaskCtx& c, List a, List b, Window w) {
+    const bool ca = is_core(c, a.v), cb = is_core(c, b.v);
+    Probe q;
+    if (ca || cb) {
+        List it, pr;
+        if (ca && cb) {            // both probe-able: iterate the shorter window
+            List a2 = clip(a, w), b2 = clip(b, w);
+            if (a2.n <= b2.n) { it = a2; pr = b; } else { it = b2; pr = a; }
+        } else if (cb) {
+            it = clip(a, w);
+            pr = b;
+        } else {
+            it = clip(b, w);
+            pr = a;
         }
-        unsigned h = __ballot_sync(kFull, hit);
-        if (c.lane == 0) acc.sub(__popc(h));
-    } else {
-        const int32_t* a; int na;
-        if (lv.src_kind == 1) nbr(c, v[lv.src], a, na);
-        else { a = c.slots + (size_t)lv.src * c.slot_cap; na = c.slen[lv.src]; }
-        int a0, a1;
-        clip(a, na, w, a0, a1);
-        bool hit = false;
-        if (c.lane < L && (lv.excl_mask >> c.lane & 1)) {
-            int x = v[c.lane];
-            hit = x > w.lo && x < w.hi && contains(a + a0, a1 - a0, x);
-        }
-        unsigned h = __ballot_sync(kFull, hit);
-        if (c.lane == 0) acc.add((unsigned long long)(a1 - a0) - __popc(h));
+        q.it = it;
+        q.pr = pr;
+        q.bitmap = true;
+        // elements of `it` at or above core_n are searched in pr from there
+        q.tail = (it.n > 0 && __ldg(it.p + it.n - 1) >= c.core_n) ? lower_bound(pr.p, pr.n, c.core_n) : pr.n;
+        return q;
+    }
+    List a2 = clip(a, w), b2 = clip(b, w);
+    if (a2.n <= b2.n) { q.it = a2; q.pr = b2; } else { q.it = b2; q.pr = a2; }
+    q.bitmap = false;
+    q.tail = 0;
+    return q;
+}
+
+__device__ __forceinline__ void tally(const TaskCtx& c, List a, List b, Window w, unsigned long long extra) {
+    if (c.sbytes) {
+        List a2 = clip(a, w), b2 = clip(b, w);
+        *c.sbytes += intersect_bytes(a2.n, b2.n) + extra;
     }
 }
 
-// Per-lane sorted intersection size: binary search of the shorter list in
-// the longer when their lengths differ a lot, a linear merge otherwise.
-__device__ __forceinline__ int lane_intersect_count(const int32_t* __restrict__ A, int na,
-                                                    const int32_t* __restrict__ B, int nb) {
-    if (na > nb) {
-        const int32_t* t = A; A = B; B = t;
-        int tn = na; na = nb; nb = tn;
+// Warp-cooperative intersection of a and b within window w. Writes the
+// (sorted) result to out when out != nullptr and returns its size
+// (warp-uniform). With acc != nullptr each lane also adds its own matches.
+__device__ __forceinline__ int warp_intersect(const TaskCtx& c, List a, List b, Window w,
+                                              int32_t* __restrict__ out, int cap, Acc* acc) {
+    const Probe q = choose(c, a, b, w);
+    const int n = q.it.n, lane = c.lane;
+    int total = 0, from = q.bitmap ? q.tail : 0;
+    for (int base = 0; base < n; base += 32) {
+        const int i = base + lane;
+        int x = 0, pos = q.pr.n;
+        bool f = false, searched = false;
+        if (i < n) {
+            x = __ldg(q.it.p + i);
+            if (q.bitmap && x < c.core_n) {
+                f = core_bit(c, q.pr.v, x);
+            } else {
+                pos = from + lower_bound(q.pr.p + from, q.pr.n - from, x);
+                f = pos < q.pr.n && __ldg(q.pr.p + pos) == x;
+                searched = true;
+            }
+        }
+        const unsigned m = __ballot_sync(kFull, f);
+        if (out && f) {
+            const int at = total + __popc(m & lanemask_lt());
+            if (at < cap) out[at] = x; else atomicExch(c.err, 2);
+        }
+        if (acc && f) acc->add(1);
+        total += __popc(m);
+        // later elements are larger: narrow the searched range
+        const int last = min(31, n - 1 - base);
+        const int lpos = __shfl_sync(kFull, pos, last);
+        if (__shfl_sync(kFull, (int)searched, last)) from = lpos;
     }
+    if (c.sbytes && lane == 0) tally(c, a, b, w, out ? 4ull * (unsigned long long)total : 0ull);
+    return total;
+}
+
+// Default work above which a lane hands its last-level count to the warp.
+constexpr int kLaneWork = 192;
+
+// Per-lane intersection size of a and b within w, or -1 when the estimated
+// work exceeds kLaneWork (nothing is counted then).
+__device__ __forceinline__ int lane_intersect_count(const TaskCtx& c, List a, List b, Window w) {
+    const Probe q = choose(c, a, b, w);
+    const int n = q.it.n;
+    if (q.bitmap) {
+        if (n > c.lane_work) return -1;
+        int cnt = 0, from = q.tail;
+        for (int i = 0; i < n; ++i) {
+            const int x = __ldg(q.it.p + i);
+            if (x < c.core_n) {
+                cnt += core_bit(c, q.pr.v, x);
+            } else {
+                from += lower_bound(q.pr.p + from, q.pr.n - from, x);
+                cnt += (from < q.pr.n && __ldg(q.pr.p + from) == x);
+            }
+        }
+        return cnt;
+    }
+    const int sh = n, lo = q.pr.n;
+    const bool search = lo > 16 * sh;
+    const int work = search ? sh * (32 - __clz(lo | 1)) : sh + lo;
+    if (work > c.lane_work) return -1;
+    if (sh == 0) return 0;
+    const int32_t* A = q.it.p;
+    const int32_t* B = q.pr.p;
     int cnt = 0;
-    if (na == 0) return 0;
-    if (nb > 16 * na) {
+    if (search) {
         int from = 0;
-        for (int i = 0; i < na && from < nb; ++i) {
-            int x = __ldg(A + i);
-            from += lower_bound(B + from, nb - from, x);
-            cnt += (from < nb && __ldg(B + from) == x);
+        for (int i = 0; i < sh && from < lo; ++i) {
+            const int x = __ldg(A + i);
+            from += lower_bound(B + from, lo - from, x);
+            cnt += (from < lo && __ldg(B + from) == x);
         }
         return cnt;
     }
@@ -249,83 +282,136 @@ __device__ __forceinline__ int lane_intersect_count(const int32_t* __restrict__ 
     for (;;) {
         if (x == y) {
             ++cnt;
-            if (++i == na || ++j == nb) break;
+            if (++i == sh || ++j == lo) break;
             x = __ldg(A + i);
             y = __ldg(B + j);
         } else if (x < y) {
-            if (++i == na) break;
+            if (++i == sh) break;
             x = __ldg(A + i);
         } else {
-            if (++j == nb) break;
+            if (++j == lo) break;
             y = __ldg(B + j);
         }
     }
     return cnt;
 }
 
-// Work above which a lane hands its last-level count to the whole warp.
-constexpr int kLaneWork = 192;
+// Is x in list a (x already inside the window a was clipped to)?
+__device__ __forceinline__ bool member(const TaskCtx& c, List a, int x) {
+    if (is_core(c, a.v) && x < c.core_n) return core_bit(c, a.v, x);
+    const int p = lower_bound(a.p, a.n, x);
+    return p < a.n && __ldg(a.p + p) == x;
+}
 
-// Per-lane version of count_last: v[] is this lane's own matched vertices.
-// Returns false (and counts nothing) when the work is large enough that the
-// warp-cooperative count_last should take it.
+__device__ __forceinline__ void run_builds(const TaskCtx& c, int d, const int* v) {
+    const GpLevel& L = c.P->lvl[d];
+    for (int q = 0; q < L.nbuild; ++q) {
+        const GpBuild& B = L.build[q];
+        const List a = (B.base_kind == 1) ? nbr(c, v[B.base]) : slot(c, B.base);
+        const Window w = window(B.lo_mask, B.hi_mask, v);
+        int32_t* out = c.slots + (size_t)B.dst * c.slot_cap;
+        const int n = warp_intersect(c, a, nbr(c, v[d]), w, out, c.slot_cap, nullptr);
+        if (c.lane == 0) c.slen[B.dst] = n;
+        __syncwarp();
+    }
+}
+
+// Matched vertices that lie in the last level's candidate set: they are not
+// new vertices (injectivity) and are subtracted from its size.
+__device__ __forceinline__ int excluded_hits(const TaskCtx& c, const GpLevel& lv, int L, const int* v,
+                                             Window w, List a, const List* b) {
+    int hits = 0;
+    for (int j = 0; j < L; ++j) {
+        if (!(lv.excl_mask >> j & 1)) continue;
+        const int x = v[j];
+        if (x > w.lo && x < w.hi && member(c, a, x) && (!b || member(c, *b, x))) ++hits;
+    }
+    return hits;
+}
+
+// Contribution of the innermost loop given v[0..k-2] (warp-uniform).
+__device__ __forceinline__ void count_last(const TaskCtx& c, const int* v, Acc& acc) {
+    const GpPlan& P = *c.P;
+    const int L = P.k - 1;
+    const GpLevel& lv = P.lvl[L];
+    const Window w = window(lv.lo_mask, lv.hi_mask, v);
+    if (P.last_count_only) {
+        const List a = (P.last_base_kind == 1) ? nbr(c, v[P.last_base]) : slot(c, P.last_base);
+        const List b = nbr(c, v[L - 1]);
+        warp_intersect(c, a, b, w, nullptr, 0, &acc);
+        if (c.lane == 0) {
+            const List a2 = is_core(c, a.v) ? a : clip(a, w);
+            const List b2 = is_core(c, b.v) ? b : clip(b, w);
+            acc.sub((unsigned long long)excluded_hits(c, lv, L, v, w, a2, &b2));
+        }
+    } else {
+        const List a = clip((lv.src_kind == 1) ? nbr(c, v[lv.src]) : slot(c, lv.src), w);
+        if (c.lane == 0) acc.add((unsigned long long)a.n - excluded_hits(c, lv, L, v, w, a, nullptr));
+    }
+}
+
+// Per-lane count_last: v[] is this lane's own matched vertices. Returns
+// false (and counts nothing) when the warp-cooperative version should run.
 __device__ __forceinline__ bool count_last_lane(const TaskCtx& c, const int* v, Acc& acc) {
     const GpPlan& P = *c.P;
     const int L = P.k - 1;
     const GpLevel& lv = P.lvl[L];
-    Window w = window(lv.lo_mask, lv.hi_mask, v);
+    const Window w = window(lv.lo_mask, lv.hi_mask, v);
     if (P.last_count_only) {
-        const int32_t* a; int na;
-        if (P.last_base_kind == 1) nbr(c, v[P.last_base], a, na);
-        else { a = c.slots + (size_t)P.last_base * c.slot_cap; na = c.slen[P.last_base]; }
-        const int32_t* b; int nb;
-        nbr(c, v[L - 1], b, nb);
-        int a0, a1, b0, b1;
-        clip(a, na, w, a0, a1);
-        clip(b, nb, w, b0, b1);
-        const int la = a1 - a0, lb = b1 - b0;
-        const int sh = min(la, lb), lo = max(la, lb);
-        const int work = (lo > 16 * sh) ? sh * (32 - __clz(lo | 1)) : la + lb;
-        if (work > kLaneWork) return false;
-        int cnt = lane_intersect_count(a + a0, la, b + b0, lb);
-        for (int j = 0; j < L; ++j) {
-            if (!(lv.excl_mask >> j & 1)) continue;
-            int x = v[j];
-            if (x > w.lo && x < w.hi && contains(a + a0, la, x) && contains(b + b0, lb, x)) --cnt;
-        }
-        acc.add((unsigned long long)cnt);
-        if (c.sbytes) *c.sbytes += intersect_bytes(la, lb);
+        const List a = (P.last_base_kind == 1) ? nbr(c, v[P.last_base]) : slot(c, P.last_base);
+        const List b = nbr(c, v[L - 1]);
+        const int cnt = lane_intersect_count(c, a, b, w);
+        if (cnt < 0) return false;
+        const List a2 = is_core(c, a.v) ? a : clip(a, w);
+        const List b2 = is_core(c, b.v) ? b : clip(b, w);
+        acc.add((unsigned long long)(cnt - excluded_hits(c, lv, L, v, w, a2, &b2)));
+        if (c.sbytes) { const List x = clip(a, w), y = clip(b, w); *c.sbytes += intersect_bytes(x.n, y.n); }
         return true;
     }
-    const int32_t* a; int na;
-    if (lv.src_kind == 1) nbr(c, v[lv.src], a, na);
-    else { a = c.slots + (size_t)lv.src * c.slot_cap; na = c.slen[lv.src]; }
-    int a0, a1;
-    clip(a, na, w, a0, a1);
-    int cnt = a1 - a0;
-    for (int j = 0; j < L; ++j) {
-        if (!(lv.excl_mask >> j & 1)) continue;
-        int x = v[j];
-        if (x > w.lo && x < w.hi && contains(a + a0, a1 - a0, x)) --cnt;
-    }
-    acc.add((unsigned long long)cnt);
+    const List a = clip((lv.src_kind == 1) ? nbr(c, v[lv.src]) : slot(c, lv.src), w);
+    acc.add((unsigned long long)(a.n - excluded_hits(c, lv, L, v, w, a, nullptr)));
     return true;
+}
+
+// Inclusion-exclusion for the last two depths (Section IV-D, k = 2): with
+// v[0..k-3] bound, the last two vertices range over S_a (depth k-2) and
+// S_b (depth k-1), minus already-matched vertices, and must differ:
+// |S_a| |S_b| - |S_a ∩ S_b|. The plan has no restriction acting at those
+// depths; the host divides the job's total by the plan's iep_div.
+__device__ __forceinline__ void iep_count(const TaskCtx& c, const int* v, Acc& acc) {
+    const GpPlan& P = *c.P;
+    const int da = P.k - 2, db = P.k - 1;
+    const GpLevel& LA = P.lvl[da];
+    const GpLevel& LB = P.lvl[db];
+    const Window wa = window(LA.lo_mask, LA.hi_mask, v), wb = window(LB.lo_mask, LB.hi_mask, v);
+    const List A = clip((LA.src_kind == 1) ? nbr(c, v[LA.src]) : slot(c, LA.src), wa);
+    const List B = clip((LB.src_kind == 1) ? nbr(c, v[LB.src]) : slot(c, LB.src), wb);
+    const Window open{-1, INT_MAX};
+    const int ab = warp_intersect(c, A, B, open, nullptr, 0, nullptr);
+    if (c.lane == 0) {
+        const int a = A.n - excluded_hits(c, LA, da, v, wa, A, nullptr);
+        const int b = B.n - excluded_hits(c, LB, db, v, wb, B, nullptr);
+        int both = 0;                     // matched vertices inside S_a ∩ S_b
+        for (int j = 0; j < da; ++j)
+            if (member(c, A, v[j]) && member(c, B, v[j])) ++both;
+        acc.add((unsigned long long)a * (unsigned long long)b);
+        acc.sub((unsigned long long)(ab - both));
+    }
 }
 
 // The loop at depth k-2 with one candidate per lane: every lane counts the
 // last level for its own candidate; candidates with heavy intersections are
 // then counted one at a time by the whole warp.
-__device__ __forceinline__ void lane_parallel_last_two(const TaskCtx& c, int* v, const int32_t* lst,
-                                                       int beg, int end, Acc& acc) {
+__device__ __forceinline__ void lane_parallel_last_two(const TaskCtx& c, int* v, List lst, Acc& acc) {
     const GpPlan& P = *c.P;
     const int d = P.k - 2;
     const uint8_t ex = P.lvl[d].excl_mask;
-    for (int base = beg; base < end; base += 32) {
+    for (int base = 0; base < lst.n; base += 32) {
         const int i = base + c.lane;
         int x = -1;
-        bool active = i < end;
+        bool active = i < lst.n;
         if (active) {
-            x = __ldg(lst + i);
+            x = __ldg(lst.p + i);
             for (int j = 0; j < d; ++j) active &= !(((ex >> j) & 1) && v[j] == x);
             if (c.sbytes) *c.sbytes += 4;
         }
@@ -344,47 +430,196 @@ __device__ __forceinline__ void lane_parallel_last_two(const TaskCtx& c, int* v,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Bitmap subtree: used when every vertex searched after v1 is restricted
+// below v1 and v1 is a core vertex. All later candidates are then core
+// vertices below v1, so a candidate set is the AND of core adjacency rows
+// (plus N(v0) scattered into a bitmap when v0 is not a core vertex), masked
+// to its restriction window, held in shared memory (bit x = vertex x). Lanes
+// work on 32-bit words; loops visit set bits in increasing order; the last
+// level is a popcount.
+
+__device__ __forceinline__ uint32_t window_bits(int w, int lo, int hi) {
+    // bits b of word w with lo < 32 w + b < hi
+    const int first = 32 * w;
+    uint32_t m = 0xffffffffu;
+    const int a = lo - first + 1;            // lowest allowed bit
+    if (a > 0) m = (a >= 32) ? 0u : (m << a);
+    const int b = hi - first;                // bits below b allowed
+    if (b < 32) m &= (b <= 0) ? 0u : ((1u << b) - 1u);
+    return m;
+}
+
+// Word w of N(v_j) restricted to the core (N(v0) comes from shared memory
+// when v0 is not a core vertex).
+__device__ __forceinline__ uint32_t operand_word(const TaskCtx& c, const int* v, int j, int w, bool n0_smem) {
+    if (j == 0 && n0_smem) return c.bm[w];
+    return __ldg(c.core_bits + (size_t)v[j] * c.core_words + w);
+}
+
+// S_d = AND of the rows of its operands, inside its window, without the
+// already-matched vertices that may lie in it.
+__device__ __forceinline__ void bitmap_build(const TaskCtx& c, const int* v, int d, int W, bool n0_smem) {
+    const GpLevel& L = c.P->lvl[d];
+    const Window win = window(L.lo_mask, L.hi_mask, v);
+    uint32_t* S = c.bm + (size_t)d * c.bm_stride;
+    for (int w = c.lane; w < W; w += 32) {
+        uint32_t x = window_bits(w, win.lo, win.hi);
+        for (int j = 0; j < d && x; ++j)
+            if (L.op_mask >> j & 1) x &= operand_word(c, v, j, w, n0_smem);
+        S[w] = x;
+    }
+    __syncwarp();
+    if (c.lane == 0)
+        for (int j = 0; j < d; ++j)
+            if ((L.excl_mask >> j & 1) && v[j] > win.lo && v[j] < win.hi && v[j] < 32 * W)
+                S[v[j] >> 5] &= ~(1u << (v[j] & 31));
+    __syncwarp();
+}
+
+// Next set bit of S_d at or after the iteration state (word, remaining bits).
+__device__ __forceinline__ int bitmap_next(const uint32_t* S, int W, int& word, uint32_t& bits) {
+    while (bits == 0) {
+        if (++word >= W) return -1;
+        bits = S[word];
+    }
+    const int b = __ffs(bits) - 1;
+    bits &= bits - 1;
+    return 32 * word + b;
+}
+
+// Every candidate x of depth k-2 (set S_{k-2}): add the size of the last
+// level's set, the AND of its operand rows in its window (which may depend
+// on x), minus matched vertices inside it.
+__device__ __forceinline__ void bitmap_last_two(const TaskCtx& c, int* v, int W, bool n0_smem, Acc& acc) {
+    const GpPlan& P = *c.P;
+    const int d = P.k - 2, L = P.k - 1;
+    const GpLevel& lv = P.lvl[L];
+    const bool uses_x = lv.op_mask >> d & 1;
+    uint32_t* PP = c.bm + (size_t)1 * c.bm_stride;      // operands other than x
+    for (int w = c.lane; w < W; w += 32) {
+        uint32_t m = 0xffffffffu;
+        for (int j = 0; j < d && m; ++j)
+            if (lv.op_mask >> j & 1) m &= operand_word(c, v, j, w, n0_smem);
+        PP[w] = m;
+    }
+    __syncwarp();
+    const uint32_t* S = c.bm + (size_t)d * c.bm_stride;
+    int word = -1;
+    uint32_t bits = 0;
+    for (;;) {
+        const int x = bitmap_next(S, W, word, bits);
+        if (x < 0) break;
+        v[d] = x;
+        const Window win = window(lv.lo_mask, lv.hi_mask, v);
+        const int w0 = max(0, (win.lo + 1) >> 5);
+        const int w1 = min(W, (win.hi == INT_MAX) ? W : ((win.hi + 31) >> 5));
+        const uint32_t* rx = c.core_bits + (size_t)x * c.core_words;
+        unsigned long long cnt = 0;
+        for (int w = w0 + c.lane; w < w1; w += 32) {
+            uint32_t m = PP[w] & window_bits(w, win.lo, win.hi);
+            if (uses_x) m &= __ldg(rx + w);
+            cnt += __popc(m);
+        }
+        acc.add(cnt);
+        if (c.lane == 0) {
+            int hits = 0;
+            for (int j = 0; j <= d; ++j) {
+                if (!(lv.excl_mask >> j & 1)) continue;
+                const int y = v[j];
+                if (y <= win.lo || y >= win.hi || y >= 32 * W) continue;
+                bool in = (PP[y >> 5] >> (y & 31)) & 1u;
+                if (in && uses_x) in = (__ldg(rx + (y >> 5)) >> (y & 31)) & 1u;
+                hits += in;
+            }
+            acc.sub((unsigned long long)hits);
+        }
+    }
+}
+
+__device__ void bitmap_task(const TaskCtx& c, int* v, Acc& acc) {
+    const GpPlan& P = *c.P;
+    const int k = P.k;
+    const int W = (v[1] + 31) >> 5;          // every later candidate is below v1
+    const bool n0_smem = v[0] >= c.core_n;
+    if (n0_smem) {                           // N(v0) ∩ [0, v1) as a bitmap
+        for (int w = c.lane; w < W; w += 32) c.bm[w] = 0u;
+        __syncwarp();
+        const List a = nbr(c, v[0]);
+        const int n = lower_bound(a.p, a.n, v[1]);
+        for (int i = c.lane; i < n; i += 32) {
+            const int x = __ldg(a.p + i);
+            atomicOr(c.bm + (x >> 5), 1u << (x & 31));
+        }
+        __syncwarp();
+    }
+    if (k == 4) {
+        bitmap_build(c, v, 2, W, n0_smem);
+        bitmap_last_two(c, v, W, n0_smem, acc);
+        return;
+    }
+    int word[GP_MAX_K];
+    uint32_t bits[GP_MAX_K];
+    int d = 2;
+    bitmap_build(c, v, 2, W, n0_smem);
+    word[2] = -1;
+    bits[2] = 0;
+    while (d >= 2) {
+        const int x = bitmap_next(c.bm + (size_t)d * c.bm_stride, W, word[d], bits[d]);
+        if (x < 0) { --d; continue; }
+        v[d] = x;
+        bitmap_build(c, v, d + 1, W, n0_smem);
+        if (d + 1 == k - 2) {
+            bitmap_last_two(c, v, W, n0_smem, acc);
+        } else {
+            ++d;
+            word[d] = -1;
+            bits[d] = 0;
+        }
+    }
+}
+
 // Remaining loops of one edge task (v0, v1).
 __device__ void run_task(const TaskCtx& c, int v0, int v1, Acc& acc) {
     const GpPlan& P = *c.P;
     const int k = P.k;
     int v[GP_MAX_K];
-    const int32_t* lst[GP_MAX_K];
-    int cur[GP_MAX_K], end[GP_MAX_K];
+    List lst[GP_MAX_K];
+    int cur[GP_MAX_K];
 #pragma unroll
     for (int i = 0; i < GP_MAX_K; ++i) v[i] = -1;
     v[0] = v0;
     v[1] = v1;
+    if (P.core_dfs && c.bm && v1 < c.core_n) { bitmap_task(c, v, acc); return; }
     run_builds(c, 1, v);
     if (k == 3) { count_last(c, v, acc); return; }
-    int d = 2;
+    if (P.iep && k == 4) { iep_count(c, v, acc); return; }
     auto prepare = [&](int dd) {
         const GpLevel& L = P.lvl[dd];
-        const int32_t* a; int na;
-        if (L.src_kind == 1) nbr(c, v[L.src], a, na);
-        else { a = c.slots + (size_t)L.src * c.slot_cap; na = c.slen[L.src]; }
-        clip(a, na, window(L.lo_mask, L.hi_mask, v), cur[dd], end[dd]);
-        lst[dd] = a;
+        lst[dd] = clip((L.src_kind == 1) ? nbr(c, v[L.src]) : slot(c, L.src), window(L.lo_mask, L.hi_mask, v));
+        cur[dd] = 0;
     };
     const bool lane_last = P.lvl[k - 2].nbuild == 0;
+    int d = 2;
     prepare(2);
     while (d >= 2) {
         if (lane_last && d == k - 2) {
-            lane_parallel_last_two(c, v, lst[d], cur[d], end[d], acc);
+            lane_parallel_last_two(c, v, lst[d], acc);
             --d;
             continue;
         }
-        if (cur[d] >= end[d]) { --d; continue; }
-        int x = __ldg(lst[d] + cur[d]);
+        if (cur[d] >= lst[d].n) { --d; continue; }
+        const int x = __ldg(lst[d].p + cur[d]);
         ++cur[d];
         if (c.sbytes && c.lane == 0) *c.sbytes += 4;
-        uint8_t ex = P.lvl[d].excl_mask;
+        const uint8_t ex = P.lvl[d].excl_mask;
         bool skip = false;
         for (int j = 0; j < d; ++j) skip |= ((ex >> j) & 1) && v[j] == x;
         if (skip) continue;
         v[d] = x;
         run_builds(c, d, v);
-        if (d == k - 2) count_last(c, v, acc);
+        if (P.iep && d == k - 3) iep_count(c, v, acc);
+        else if (d == k - 2) count_last(c, v, acc);
         else { ++d; prepare(d); }
     }
 }
@@ -394,8 +629,10 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks)
 k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
         unsigned long long* __restrict__ cursor, unsigned long long* __restrict__ results,
         int32_t* __restrict__ slot_pool, int64_t warp_elems, int chunk, long long budget,
-        int* __restrict__ err, unsigned long long* __restrict__ stats) {
+        int* __restrict__ err, unsigned long long* __restrict__ stats, int lane_work, int use_core,
+        int bm_stride, int bm_sets) {
     unsigned long long my_bytes = 0;
+    extern __shared__ uint32_t s_bitmaps[];   // bm_sets x bm_stride words per warp (may be empty)
     __shared__ GpPlan s_plan[kWarps];
     __shared__ int s_len[kWarps][GP_MAX_SLOTS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -404,10 +641,16 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
     c.P = &s_plan[w];
     c.slots = slot_pool + gw * warp_elems;
     c.slen = s_len[w];
+    c.bm_stride = bm_stride;
+    c.bm = (bm_stride > 0 && !kStats) ? s_bitmaps + (size_t)w * bm_sets * bm_stride : nullptr;
     c.lane = lane;
+    c.lane_work = lane_work;
     c.err = err;
     c.row_ptr = nullptr;
     c.col = nullptr;
+    c.core_bits = nullptr;
+    c.core_n = 0;
+    c.core_words = 0;
     c.slot_cap = 0;
     c.n_vertices = 0;
     c.sbytes = kStats ? &my_bytes : nullptr;
@@ -457,6 +700,13 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
                 job_begin = J.task_begin;
                 c.row_ptr = J.row_ptr;
                 c.col = J.col;
+                c.core_bits = J.core_bits;
+                c.core_n = (use_core && J.core_bits) ? J.core_n : 0;
+                if (c.core_n == 0 || J.core_words > c.bm_stride) c.bm = nullptr;
+                else if (bm_stride > 0 && !kStats && J.plan.k - 1 <= bm_sets)
+                    c.bm = s_bitmaps + (size_t)w * bm_sets * bm_stride;
+                else c.bm = nullptr;
+                c.core_words = J.core_words;
                 c.slot_cap = J.slot_cap;
                 c.n_vertices = J.n;
             }
@@ -531,10 +781,13 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
 namespace {
 
 using KernelFn = void (*)(const CountJob*, int, int64_t, unsigned long long*, unsigned long long*,
-                          int32_t*, int64_t, int, long long, int*, unsigned long long*);
+                          int32_t*, int64_t, int, long long, int*, unsigned long long*, int, int, int, int);
 
 struct Geometry {
     KernelFn kern;
+    int bm_stride;          // words per bitmap set (0: no bitmap subtree)
+    int bm_sets;            // bitmap sets per warp (k - 1 of the largest such plan)
+    size_t smem;            // dynamic shared memory per block
     int64_t blocks;
     int64_t warp_elems;     // scratch elements per warp
     size_t per_block;       // scratch bytes per block
@@ -555,13 +808,27 @@ gp_status geometry(const CountJob* jobs, int njobs, const LaunchOpts& opt, Geome
     GP_CUDA_TRY(cudaGetDevice(&dev));
     GP_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     int occ = 0;
-    // two register budgets: 64 registers (4 blocks per SM, the default: the
-    // kernel is latency-bound and gains more from warps than from registers)
-    // or about 96 (2 blocks per SM, when 1 or 2 blocks per SM are asked for)
-    const bool dense = !(opt.blocks_per_sm == 1 || opt.blocks_per_sm == 2);
-    g->kern = opt.stats ? (dense ? k_count<true, 4> : k_count<true, 1>)
-                        : (dense ? k_count<false, 4> : k_count<false, 1>);
-    GP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, g->kern, kWarps * 32, 0));
+    // three register budgets: 64 registers (4 blocks per SM, the default: the
+    // kernel is latency-bound and gains more from warps than from registers),
+    // 85 (3 blocks per SM) or about 100 (2 blocks per SM), chosen by the
+    // requested blocks per SM
+    const int want = opt.blocks_per_sm;
+    if (want == 1 || want == 2) g->kern = opt.stats ? k_count<true, 1> : k_count<false, 1>;
+    else if (want == 3) g->kern = opt.stats ? k_count<true, 3> : k_count<false, 3>;
+    else g->kern = opt.stats ? k_count<true, 4> : k_count<false, 4>;
+    // bitmap sets in shared memory when some job may search a core subtree
+    g->bm_stride = 0;
+    g->bm_sets = 0;
+    if (!opt.stats && !opt.no_core)
+        for (int j = 0; j < njobs; ++j)
+            if (jobs[j].plan.core_dfs && jobs[j].core_bits && jobs[j].core_n > 0) {
+                g->bm_stride = std::max(g->bm_stride, (int)jobs[j].core_words);
+                g->bm_sets = std::max(g->bm_sets, jobs[j].plan.k - 1);
+            }
+    g->smem = (size_t)kWarps * (size_t)g->bm_sets * (size_t)g->bm_stride * sizeof(uint32_t);
+    if (g->smem > 48 * 1024)
+        GP_CUDA_TRY(cudaFuncSetAttribute(g->kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem));
+    GP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, g->kern, kWarps * 32, g->smem));
     int per_sm = opt.blocks_per_sm > 0 ? std::min(opt.blocks_per_sm, occ) : occ;
     if (per_sm < 1) per_sm = 1;
     g->blocks = (int64_t)nsm * per_sm;
@@ -629,9 +896,10 @@ gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& opt, cuda
     if (e == cudaSuccess) e = cudaMemsetAsync(d_res, 0, res_b, st);
     if (e == cudaSuccess && ev0) e = cudaEventRecord(ev0, st);
     if (e == cudaSuccess && total > 0) {
-        kern<<<(unsigned)blocks, kWarps * 32, 0, st>>>(d_jobs, njobs, total, d_cursor, d_res, d_slots,
+        kern<<<(unsigned)blocks, kWarps * 32, geo.smem, st>>>(d_jobs, njobs, total, d_cursor, d_res, d_slots,
                                                       warp_elems, chunk, (long long)opt.budget_cycles,
-                                                      d_err, d_stats);
+                                                      d_err, d_stats, opt.lane_work > 0 ? opt.lane_work : kLaneWork,
+                                                      opt.no_core ? 0 : 1, geo.bm_stride, geo.bm_sets);
         count_launch();
         e = cudaGetLastError();
     }
@@ -708,7 +976,7 @@ gp_status run_count_in_scratch(const CountJob* jobs, int njobs, void* d_scratch,
     GP_CUDA_TRY(cudaMemsetAsync(d_res, 0, words_b, st));       // results, cursor, error word start at 0
     if (total > 0) {
         kern<<<(unsigned)blocks, kWarps * 32, 0, st>>>(d_jobs, njobs, total, d_cursor, d_res, d_slots,
-                                                      warp_elems, chunk, 0, d_err, d_stats);
+                                                      warp_elems, chunk, 0, d_err, d_stats, kLaneWork, 1, 0, 0);
         count_launch();
         GP_CUDA_TRY(cudaGetLastError());
     }

@@ -21,6 +21,9 @@ struct gp_graph {
                                   // >= kHeavyDegree (degree-ordered graphs only)
     int64_t* row_ptr = nullptr;   // device, n + 1
     int32_t* col = nullptr;       // device, nnz
+    uint32_t* core_bits = nullptr;  // device, core_n x core_words: adjacency among
+    int32_t core_n = 0;             // the core_n highest-degree vertices (ids
+    int32_t core_words = 0;         // 0..core_n-1 of a degree-ordered graph)
     int32_t* perm = nullptr;      // device, n (new id -> input id) or null
     std::mutex mu;
     bool tri_done = false;
@@ -40,6 +43,8 @@ gp_status csr_to_pairs(const int64_t* d_row_ptr, const int32_t* d_col, int32_t n
                        int32_t* d_src, int32_t* d_dst, cudaStream_t st);
 // Maximum degree of a device CSR (graph.cu).
 gp_status max_degree(const int64_t* d_row_ptr, int32_t n, cudaStream_t st, int32_t* out);
+// Adjacency bit matrix of vertices [0, core_n) among themselves (graph.cu).
+gp_status build_core_bits(gp_graph* g, int32_t core_n, cudaStream_t st);
 // First CSR entry of the first vertex whose degree is below min_deg, for a
 // graph whose degrees do not increase with the id (graph.cu).
 gp_status heavy_prefix(const int64_t* d_row_ptr, int32_t n, int32_t min_deg, cudaStream_t st,
@@ -56,7 +61,14 @@ struct CountJob {
     int64_t ntasks;          // edge tasks of this job
     int64_t task_offset;     // first global task index of this job
     int64_t heavy;           // leading tasks of this job handed out one at a time
+    const uint32_t* core_bits;  // core adjacency bit matrix (null: none)
+    int32_t core_n;
+    int32_t core_words;
 };
+
+// Largest core (in vertices) whose adjacency bit matrix a graph keeps:
+// 8192 x 8192 bits = 8 MB.
+constexpr int32_t kCoreMax = 8192;
 
 // Vertices of at least this degree start tasks heavy enough to be handed out
 // one per grab (degree-ordered graphs put them first).
@@ -68,6 +80,8 @@ struct LaunchOpts {
     int chunk = 0;           // 0 = automatic
     int64_t budget_cycles = 0;
     bool stats = false;      // instrumented kernel that tallies algorithmic bytes
+    bool no_core = false;    // binary searches only (no core bit matrix)
+    int lane_work = 0;       // 0 = default
 };
 
 // Run the jobs in one persistent launch. results[2 j], results[2 j + 1]
@@ -76,9 +90,6 @@ struct LaunchOpts {
 gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& lo, cudaStream_t st,
                     uint64_t* results, int64_t* processed, float* kernel_ms = nullptr,
                     uint64_t* algo_bytes = nullptr);
-
-// Device scratch run_count would allocate for these jobs and options.
-gp_status scratch_bytes(const CountJob* jobs, int njobs, const LaunchOpts& lo, uint64_t* bytes);
 
 // run_count without allocating: results, job table and intermediate sets all
 // live in the caller's device buffer d_scratch (256-byte aligned); the grid
@@ -90,6 +101,12 @@ gp_status run_count_in_scratch(const CountJob* jobs, int njobs, void* d_scratch,
 // The job of plan idx of s over all edge tasks of g, with g's device made
 // current (capi.cu).
 gp_status single_job(gp_graph* g, const gp_schedules* s, int32_t idx, CountJob* job);
+// A job's count from its 128-bit device total (inclusion-exclusion plans are
+// divided by their multiplicity); GP_ERR_OVERFLOW beyond 64 bits (capi.cu).
+gp_status job_total(const CountJob& job, const uint64_t* res, uint64_t* out);
+
+// Device scratch run_count would allocate for these jobs and options.
+gp_status scratch_bytes(const CountJob* jobs, int njobs, const LaunchOpts& lo, uint64_t* bytes);
 
 }  // namespace gp
 

@@ -5,6 +5,8 @@
 // Each directed pair (u, v) travels as one 64-bit key (u << 32) | v, so a
 // single radix sort orders the pairs by source and then by target, which is
 // exactly the CSR order. The sort and the unique pass are CUB library calls.
+#include <algorithm>
+
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_select.cuh>
 
@@ -178,7 +180,48 @@ __global__ void k_heavy_prefix(const int64_t* __restrict__ row_ptr, int32_t n, i
     *out = row_ptr[lo];
 }
 
+// One warp per core vertex u: set bit x of row u for every neighbour x of u
+// below core_n (a prefix of u's sorted list).
+__global__ void k_core_bits(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                            int32_t core_n, int32_t words, uint32_t* __restrict__ bits) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < core_n;
+         u += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t b = row_ptr[u], e = row_ptr[u + 1];
+        for (int64_t i = b + lane; i < e; i += 32) {
+            const int32_t x = col[i];
+            if (x >= core_n) break;
+            atomicOr(bits + u * words + (x >> 5), 1u << (x & 31));
+        }
+    }
+}
+
 }  // namespace
+
+gp_status build_core_bits(gp_graph* g, int32_t core_n, cudaStream_t st) {
+    if (core_n <= 0) return GP_OK;
+    const int32_t words = (core_n + 31) / 32;
+    const size_t bytes = sizeof(uint32_t) * (size_t)core_n * (size_t)words;
+    uint32_t* bits = nullptr;
+    GP_CUDA_TRY(cudaMalloc(&bits, bytes));
+    cudaError_t e = cudaMemsetAsync(bits, 0, bytes, st);
+    if (e == cudaSuccess) {
+        const int blocks = (int)std::min<int64_t>(((int64_t)core_n * 32 + kThreads - 1) / kThreads, 4096);
+        k_core_bits<<<blocks, kThreads, 0, st>>>(g->row_ptr, g->col, core_n, words, bits);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaFree(bits);
+        set_error("core bit matrix: %s", cudaGetErrorString(e));
+        return GP_ERR_CUDA;
+    }
+    g->core_bits = bits;
+    g->core_n = core_n;
+    g->core_words = words;
+    return GP_OK;
+}
 
 gp_status heavy_prefix(const int64_t* d_row_ptr, int32_t n, int32_t min_deg, cudaStream_t st,
                        int64_t* out) {
@@ -319,7 +362,9 @@ gp_status build_graph(const int32_t* d_src, const int32_t* d_dst, int64_t m, int
     rc = keys_to_csr(keys_a.as<uint64_t>(), nnz, n, st, g);
     if (rc != GP_OK) { cudaFree(new2old); return rc; }
     g->perm = new2old;
-    return heavy_prefix(g->row_ptr, n, kHeavyDegree, st, &g->heavy_end);
+    rc = heavy_prefix(g->row_ptr, n, kHeavyDegree, st, &g->heavy_end);
+    if (rc != GP_OK) return rc;
+    return build_core_bits(g, std::min(n, kCoreMax), st);
 }
 
 }  // namespace gp

@@ -67,7 +67,9 @@ extern "C" gp_status gp_count_noalloc(gp_graph* g, const gp_schedules* s, int32_
     uint64_t res[2] = {0, 0};
     rc = gp::run_count_in_scratch(&job, 1, scratch, kNoallocScratchBytes, static_cast<cudaStream_t>(stream), res);
     if (rc != GP_OK) return rc;
-    if (res[1]) { gp::set_error("count does not fit in 64 bits"); return GP_ERR_OVERFLOW; }
-    *out = res[0];
+    uint64_t total = 0;
+    rc = gp::job_total(job, res, &total);
+    if (rc != GP_OK) return rc;
+    *out = total;
     return GP_OK;
 }

@@ -33,7 +33,8 @@ struct GpLevel {
     uint8_t hi_mask;   // candidate < v_j
     uint8_t excl_mask; // earlier depths whose vertex may lie in the set (injectivity)
     int8_t nbuild;     // builds executed after v_d is bound
-    int8_t pad[2];
+    uint8_t op_mask;   // depths whose neighbourhoods are intersected for this set
+    int8_t pad[1];
     GpBuild build[GP_MAX_BUILDS];
 };
 
@@ -48,5 +49,15 @@ struct GpPlan {
     int16_t last_base;
     int8_t order[GP_MAX_K];   // pattern vertex searched at depth d
     int8_t pad[1];
+    // Inclusion-exclusion counting of the last two (non-adjacent) depths
+    // (Section IV-D with k = 2): at depth k-3 the contribution is
+    // |S_{k-2}| |S_{k-1}| - |S_{k-2} ∩ S_{k-1}|; restrictions acting at the
+    // last two depths are dropped, and the job's total is divided by iep_div.
+    int32_t iep;
+    uint32_t iep_div;
+    // 1 when every vertex searched after depth 1 is restricted below v_1:
+    // if v_1 is a core vertex the whole remaining search stays among core
+    // vertices and runs on their adjacency bit matrix.
+    int32_t core_dfs;
     GpLevel lvl[GP_MAX_K];
 };

@@ -358,6 +358,7 @@ bool compile_plan(const PatternInfo& p, const int8_t* sched, ResMask res, GpPlan
         if (nops == 0) { err = "schedule prefix is not connected (phase 1)"; return false; }
         L.lo_mask = lo;
         L.hi_mask = hi;
+        L.op_mask = opmask;
         L.excl_mask = (uint8_t)(((1u << x) - 1) & ~opmask & ~lo & ~hi);
         if (nops == 1) { L.src_kind = 1; L.src = (int8_t)ops[0]; continue; }
         int prev_slot = -1;
@@ -395,7 +396,60 @@ bool compile_plan(const PatternInfo& p, const int8_t* sched, ResMask res, GpPlan
         }
     }
     plan.nslots = nslots;
+    plan.core_dfs = k >= 4;
+    for (int x = 2; x < k; ++x)
+        if (!gt[1][x]) plan.core_dfs = 0;      // some later vertex may exceed v_1
     *out = plan;
+    return true;
+}
+
+bool iep_divisor(const PatternInfo& p, const int8_t* sched, ResMask res, ResMask* outer, uint32_t* div) {
+    const int k = p.k;
+    if (k < 4 || p.adj[sched[k - 1]][sched[k - 2]]) return false;
+    int pos[GP_MAX_K];
+    for (int i = 0; i < k; ++i) pos[sched[i]] = i;
+    ResMask ro = 0;
+    for (ResMask m = res; m; m &= m - 1) {
+        const int bit = __builtin_ctzll(m);
+        if (std::max(pos[bit / GP_MAX_K], pos[bit % GP_MAX_K]) <= k - 3) ro |= 1ull << bit;
+    }
+    const OrderTable& t = order_table(k);
+    long mult = -1;
+    for (int o = 0; o < t.n; ++o) {             // rank pattern pi of the images
+        const auto& pi = t.perms[o];
+        long c = 0;
+        for (const Perm& sg : p.auts) {         // maps f o sigma, sigma in Aut
+            bool ok = true;
+            for (ResMask m = ro; m && ok; m &= m - 1) {
+                const int bit = __builtin_ctzll(m);
+                ok = pi[sg[bit / GP_MAX_K]] > pi[sg[bit % GP_MAX_K]];
+            }
+            c += ok;
+        }
+        if (mult < 0) mult = c;
+        else if (c != mult) return false;
+    }
+    if (mult <= 0) return false;
+    *outer = ro;
+    *div = (uint32_t)mult;
+    return true;
+}
+
+bool compile_plan_iep(const PatternInfo& p, const int8_t* sched, ResMask res, GpPlan* out,
+                      std::string& err) {
+    ResMask ro = 0;
+    uint32_t div = 0;
+    if (!iep_divisor(p, sched, res, &ro, &div)) {
+        err = "inclusion-exclusion does not apply to this configuration";
+        return false;
+    }
+    if (!compile_plan(p, sched, ro, out, err)) return false;
+    const int k = p.k;
+    out->iep = 1;
+    out->iep_div = div;
+    out->core_dfs = 0;
+    // depth k-2 is not bound when the last set is counted
+    out->lvl[k - 1].excl_mask &= (uint8_t)~(1u << (k - 2));
     return true;
 }
 

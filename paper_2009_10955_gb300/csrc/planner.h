@@ -61,6 +61,19 @@ int upper_bound_restrictions(const int8_t* sched, ResMask res, int k);
 bool compile_plan(const PatternInfo& p, const int8_t* sched, ResMask res, GpPlan* out,
                   std::string& err);
 
+// Inclusion-exclusion over the last two depths (Section IV-D, k = 2):
+// applicable when k >= 4 and the last two searched vertices are not adjacent.
+// The restrictions whose later endpoint is one of them are dropped; every
+// embedding is then found once per automorphism sigma whose relabelled map
+// still obeys the remaining ("outer") restrictions. Dividing by that number
+// is exact only if it is the same for all k! relative orders of the
+// vertices; *div receives it and the call returns false when it varies.
+bool iep_divisor(const PatternInfo& p, const int8_t* sched, ResMask res, ResMask* outer, uint32_t* div);
+
+// compile_plan for the inclusion-exclusion form (false when not applicable).
+bool compile_plan_iep(const PatternInfo& p, const int8_t* sched, ResMask res, GpPlan* out,
+                      std::string& err);
+
 struct Config {
     double cost;
     Perm sched;

@@ -1,0 +1,56 @@
+"""Autotuner: every launch configuration it tries gives the same counts,
+and the chosen configuration reproduces the oracle's count."""
+
+import json
+
+import pytest
+
+import oracle
+from synth import named_pattern, workload_edges
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_10955_gb300 import native
+    N = native()
+    graphs = {}
+    for name in ("rmat10", "er2000"):
+        n, s, d = workload_edges(name)
+        graphs[name] = (N.gp_graph_create_edges(s, d, n, N.GP_DEGREE_ORDER), oracle.build_csr(n, s, d))
+    return N, graphs
+
+
+def test_knobs_do_not_change_counts(env):
+    N, graphs = env
+    for gname, pname in (("rmat10", "triangle"), ("rmat10", "k4"), ("er2000", "house"), ("er2000", "k4")):
+        g, ref = graphs[gname]
+        adj = named_pattern(pname)
+        sc = N.gp_schedule(N.gp_pattern_create(adj), g)
+        expect = oracle.count(adj, ref)
+        for bps in (2, 3, 4):
+            for lane_work in (1, 64, 100000):
+                for flags in (0, N.GP_COUNT_NO_CORE):
+                    for chunk in (0, 1, 7):
+                        o = N.make_opts(blocks_per_sm=bps, lane_work=lane_work, flags=flags, chunk=chunk)
+                        assert N.gp_count(g, sc, 0, o) == (N.GP_OK, expect), (pname, bps, lane_work, flags, chunk)
+
+
+def test_tune_returns_and_caches(env, tmp_path):
+    from paper_2009_10955_gb300 import autotune
+    N, graphs = env
+    g, ref = graphs["rmat10"]
+    adj = named_pattern("k4")
+    sc = N.gp_schedule(N.gp_pattern_create(adj), g)
+    cache = str(tmp_path / "tune.json")
+    space = {"blocks_per_sm": [2, 4], "lane_work": [64, 192], "core": [True, False], "chunk": [0]}
+    best, table = autotune.tune(g, sc, 0, space=space, windows=16, width=256, cache_path=cache)
+    assert len(table) == 8 and best in [c for c, _ in table]
+    best2, _ = autotune.tune(g, sc, 0, space=space, cache_path=cache)
+    assert best2 == best
+    assert json.load(open(cache))
+    assert N.gp_count(g, sc, 0, autotune.opts_for(best)) == (N.GP_OK, oracle.count(adj, ref))

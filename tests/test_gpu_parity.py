@@ -160,6 +160,29 @@ def test_batch_across_graphs(N):
     assert list(out) == [oracle.count(adj, ra), oracle.count(adj, rb), oracle.count(adj, ra)]
 
 
+@pytest.mark.parametrize("pname", ["k4", "triangle", "k5"])
+def test_partial_core_graph(N, pname):
+    """A graph larger than the 8192-vertex core: tasks whose second vertex
+    is a core vertex run on the bit matrix, the others on lists. Whole
+    counts against the restricted oracle (k4, triangle); for k5, whole
+    counts with and without the bit matrix, and sampled roots against the
+    oracle."""
+    g, ref = graph_pair(N, "rmat14")
+    adj = named_pattern(pname)
+    s = N.gp_schedule(N.gp_pattern_create(adj), g)
+    order, res, _ = s.get(0)
+    got = N.gp_count(g, s)
+    no_core = N.gp_count(g, s, 0, N.make_opts(flags=N.GP_COUNT_NO_CORE))
+    assert got == no_core
+    if pname != "k5":
+        assert got[1] == oracle.count_restricted(adj, order, res, ref)
+    else:
+        for r in [1, 7, 40, 300, 2000, 8191, 8192, 9000, 12000]:
+            o = N.make_opts(task_begin=int(ref.row_ptr[r]), task_end=int(ref.row_ptr[r + 1]))
+            expect = oracle.count_restricted(adj, order, res, ref, root_begin=r, root_end=r + 1)
+            assert N.gp_count(g, s, 0, o)[1] == expect, r
+
+
 def test_degree_order_invariance(N):
     for name in ["rmat10", "er2000"]:
         g1, _ = graph_pair(N, name, degree_order=True)
@@ -236,7 +259,7 @@ def _sampled_rows(ref, count, seed):
     return sorted(pick)
 
 
-@pytest.mark.parametrize("pname", ["triangle", "k4", "house"])
+@pytest.mark.parametrize("pname", ["triangle", "k4", "house", "k5", "diamond"])
 def test_rmat20_sampled_roots(N, pname):
     """Full-size R-MAT scale-20 graph: the CSR is bit-exact, and for sampled
     root vertices the count of the tasks rooted there equals the oracle's

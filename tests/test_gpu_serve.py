@@ -61,13 +61,13 @@ def test_late_arrivals_join_running_batch(env):
     from paper_2009_10955_gb300.serve import Server
     N, graphs, refs = env
     srv = Server(graphs, slice_ms=0.5)
-    first = srv.submit("rmat10", named_pattern("house"))
+    first = srv.submit("rmat8", named_pattern("house"))
     time.sleep(0.01)
     late = [srv.submit("er2000", named_pattern("c4")), srv.submit("rmat8", named_pattern("k4"))]
     for r in [first] + late:
         assert r.done.wait(120) and r.error is None
     srv.close()
-    assert first.count == oracle.count(named_pattern("house"), refs["rmat10"])
+    assert first.count == oracle.count(named_pattern("house"), refs["rmat8"])
     assert late[0].count == oracle.count(named_pattern("c4"), refs["er2000"])
     assert late[1].count == oracle.count(named_pattern("k4"), refs["rmat8"])
 
