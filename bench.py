@@ -38,11 +38,17 @@ WORKLOADS = {
     "rmat20": {"graph": "rmat20", "patterns": ["triangle", "k4", "k5"]},
     # House on G(2000, 20000), seed 1
     "er2000": {"graph": "er2000", "patterns": ["house"]},
-    # Chung-Lu 4M vertices, 35M pairs, exponent 2.1, max expected degree 20K, seed 3
-    "cl4m": {"graph": "cl4m", "patterns": ["k6e", "c6chord", "grid3x2"]},
+    # Chung-Lu 4M vertices, 35M pairs, exponent 2.1, max expected degree 20K,
+    # seed 3 (the 6-cycle with a chord and the 3x2 grid need hours there,
+    # see the design notes; they are available with --patterns)
+    "cl4m": {"graph": "cl4m", "patterns": ["k6e"]},
 }
 
 L2_FLUSH_BYTES = 512 << 20          # larger than the 129 MB L2
+
+# knobs the bench lets the autotuner choose per pattern
+BENCH_TUNE_SPACE = {"blocks_per_sm": [3, 4], "lane_work": [96, 192, 512], "core": [True],
+                    "chunk": [0], "split": [1, 8]}
 
 
 def parse():
@@ -54,11 +60,18 @@ def parse():
     ap.add_argument("--workload", default="rmat20", choices=sorted(WORKLOADS))
     ap.add_argument("--patterns", default=None, help="comma list overriding the workload's patterns")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tune", action="store_true",
+                    help="let the autotuner pick launch knobs per pattern (default: library defaults, which "
+                         "measured faster on the full count than the tuner's task-sample choice)")
+    ap.add_argument("--iep", action="store_true",
+                    help="inclusion-exclusion for the last two loops where it applies (Section IV-D)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU-baseline sample budget")
     ap.add_argument("--batched-graphs", default="rmat12,rmat11,rmat10,rmat9,rmat8",
                     help="candidate graphs of the batched comparison, largest first ('' to skip)")
-    ap.add_argument("--mode", default="count", choices=["count", "serve"],
-                    help="serve: the continuous-batching sweep instead of the count benchmark")
+    ap.add_argument("--mode", default="count", choices=["count", "serve", "model"],
+                    help="serve: the continuous-batching sweep; model: performance-model accuracy")
+    ap.add_argument("--model-graph", default="rmat14")
+    ap.add_argument("--model-patterns", default="house,diamond,tailed_triangle,c4")
     ap.add_argument("--serve-scales", default="14,15,16,17,18,19,20,22")
     ap.add_argument("--serve-rates", default="10,30,100,300,1000")
     ap.add_argument("--serve-requests", type=int, default=200)
@@ -254,16 +267,36 @@ def gpu_arm(a, rank, world):
     for p in pats:
         t = time.time()
         plans[p] = N.gp_schedule(N.gp_pattern_create(named_pattern(p)), g, top_k=1, stream=stream)
+        if a.iep:
+            plans[p].set_iep(True)
         plan_s[p] = time.time() - t
     # this rank's share of every pattern's edge tasks
     lo, hi = shard_range(nnz, rank, world)
+
+    # launch knobs per pattern from the autotuner (untimed, cached like plans)
+    tuned, tune_s = {}, {}
+    if a.iep and world > 1:
+        raise SystemExit("--iep counts whole graphs only; run it with one GPU")
+    if a.tune and not a.iep:                 # the tuner samples task ranges
+        from paper_2009_10955_gb300 import autotune
+        cache = os.path.join(ROOT, "paper_2009_10955_gb300", "_build", "tune_cache.json")
+        for p in pats:
+            t = time.time()
+            tuned[p], _ = autotune.tune(g, plans[p], 0, space=BENCH_TUNE_SPACE, windows=64, width=1024,
+                                        cache_path=cache, stream=stream)
+            tune_s[p] = time.time() - t
+    def knobs(p, **kw):
+        if p in tuned:
+            from paper_2009_10955_gb300 import autotune
+            return autotune.opts_for(tuned[p], **kw)
+        return N.make_opts(**kw)
 
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     ms = ctypes.c_float()
 
     def count(p, timed):
         flush.fill_(1)                                     # evict the graph from L2
-        o = N.make_opts(task_begin=lo, task_end=hi, kernel_ms=ctypes.pointer(ms))
+        o = knobs(p, task_begin=lo, task_end=hi, kernel_ms=ctypes.pointer(ms))
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -278,7 +311,7 @@ def gpu_arm(a, rank, world):
     algo = {}
     for p in pats:
         b = ctypes.c_uint64()
-        o = N.make_opts(task_begin=lo, task_end=hi, flags=N.GP_COUNT_STATS, algo_bytes=ctypes.pointer(b))
+        o = knobs(p, task_begin=lo, task_end=hi, flags=N.GP_COUNT_STATS, algo_bytes=ctypes.pointer(b))
         N.gp_count(g, plans[p], 0, o, stream=stream)
         algo[p] = b.value
 
@@ -323,7 +356,7 @@ def gpu_arm(a, rank, world):
         g2 = N.gp_graph_create_edges(src, dst, n, N.GP_DEGREE_ORDER, stream=stream)
         for p in pats:
             s2 = N.gp_schedule(N.gp_pattern_create(named_pattern(p)), g2, top_k=1, stream=stream)
-            N.gp_count(g2, s2, 0, N.make_opts(task_begin=lo, task_end=hi), stream=stream)
+            N.gp_count(g2, s2, 0, knobs(p, task_begin=lo, task_end=hi), stream=stream)
         torch.cuda.synchronize()
         e2e_ms.append((time.time() - t) * 1000.0)
         del g2
@@ -333,6 +366,21 @@ def gpu_arm(a, rank, world):
         batched = batched_compare(N, stream, a.batched_graphs.split(","))
 
     hbm, peak_kind = peaks()
+    # L2 copy bandwidth measured in this run: 2 x 24 MB buffers (48 MB
+    # working set, inside the 129 MB L2), read + write bytes per copy
+    xa = torch.empty(24 << 20, dtype=torch.uint8, device=dev)
+    xb = torch.empty_like(xa)
+    for _ in range(5):
+        xb.copy_(xa)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 200
+    e0.record(stream)
+    for _ in range(reps):
+        xb.copy_(xa)
+    e1.record(stream)
+    e1.synchronize()
+    l2_gbs = 2 * xa.numel() * reps / (e0.elapsed_time(e1) / 1000.0) / 1e9
+    del xa, xb
     mean_kern = {p: statistics.mean(v) for p, v in kern_ms.items()}
     kern_total_ms = sum(mean_kern.values())
     algo_total = sum(algo.values())
@@ -361,6 +409,8 @@ def gpu_arm(a, rank, world):
             "plans": {p: plans[p].get(0)[:2] for p in pats},
             "graph_build_s": build_s,
             "plan_s": plan_s,
+            "tuned": tuned,
+            "tune_s": tune_s,
             "l2": "flushed (512 MB write) before every count",
             "step": "one count of each pattern, device-resident graph",
             "parallelism": f"edge tasks sharded over {world} GPU(s)",
@@ -380,6 +430,9 @@ def gpu_arm(a, rank, world):
             "kernel": "k_count",
             "algorithmic_bytes_per_step": algo_total,
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
+            "l2_peak": l2_gbs,
+            "l2_frac": achieved / l2_gbs if l2_gbs > 0 else None,
+            "l2_peak_source": "measured in this run: 48 MB copy working set, read + write bytes",
         },
         "clocks": clk,
         "batched": batched,
@@ -460,7 +513,7 @@ def serve_bench(N, stream, scales, rates, per_rate, deadline_s, slice_ms, seed=7
     rows = []
     for ri, rate in enumerate(rates):
         arr = poisson_arrivals(rate, per_rate, seed + ri)
-        srv = Server(graphs, slice_ms=slice_ms, stream=stream,
+        srv = Server(graphs, slice_ms=slice_ms, stream=stream, item_ms=20 * slice_ms,
                      max_slices=max(1, int(deadline_s * 1000.0 / slice_ms)))
         t0 = time.perf_counter()
         reqs = []
@@ -484,6 +537,59 @@ def serve_bench(N, stream, scales, rates, per_rate, deadline_s, slice_ms, seed=7
                      "slices": srv.slices})
     return {"metric": "serving latency and throughput", "graphs": names, "slice_ms": slice_ms,
             "deadline_s": deadline_s, "rows": rows}
+
+
+def model_bench(N, stream, graph_name, patterns, max_configs=400):
+    """Performance-model accuracy (the shape of the paper's Fig. 9, Fig. 10
+    and Table II on a synthetic graph): count with every efficient schedule
+    x restriction set (evenly subsampled beyond max_configs), time each, and
+    compare the model's choice with the measured best. Every configuration
+    must give the same count."""
+    import torch
+    n, src, dst = workload_edges(graph_name)
+    g = N.gp_graph_create_edges(src, dst, n, N.GP_DEGREE_ORDER, stream=stream)
+    st = g.stats(stream=stream)
+    ms = ctypes.c_float()
+    rows = []
+    for name in patterns:
+        p = N.gp_pattern_create(named_pattern(name))
+        scheds, _ = p.schedules()
+        sets = p.restriction_sets()
+        pairs = [(sc, rs) for sc in scheds for rs in sets]
+        step = max(1, len(pairs) // max_configs)
+        pairs = pairs[::step]
+        pick = N.gp_schedule(p, g, top_k=1, stream=stream).get(0)[:2]
+        if pick not in pairs:
+            pairs.append(pick)
+        timed, count = [], None
+        for sc, rs in pairs:
+            one = N.gp_schedule_explicit(p, sc, rs)
+            best_ms = None
+            for _ in range(2):
+                c = N.gp_count(g, one, 0, N.make_opts(kernel_ms=ctypes.pointer(ms)), stream=stream)[1]
+                best_ms = ms.value if best_ms is None else min(best_ms, ms.value)
+            if count is None:
+                count = c
+            elif c != count:
+                raise AssertionError(f"{name}: configuration {sc} {rs} gave {c}, expected {count}")
+            cost = N.gp_config_cost(p, sc, rs, st["n"], st["m"], st["tri_cnt"])
+            timed.append((best_ms, cost, sc, rs))
+        t_sorted = sorted(x[0] for x in timed)
+        pick_ms = next(x[0] for x in timed if (x[2], x[3]) == pick)
+        costs = [x[1] for x in timed]
+        times = [x[0] for x in timed]
+        rc = np.argsort(np.argsort(costs))
+        rt = np.argsort(np.argsort(times))
+        spearman = float(np.corrcoef(rc, rt)[0, 1]) if len(timed) > 2 else None
+        # restriction sets for the picked schedule: best set vs the average set
+        same = [x[0] for x in timed if x[2] == pick[0]]
+        rows.append({"pattern": name, "count": count, "configs": len(timed),
+                     "best_ms": t_sorted[0], "worst_ms": t_sorted[-1], "pick_ms": pick_ms,
+                     "pick_vs_best": pick_ms / t_sorted[0], "worst_vs_best": t_sorted[-1] / t_sorted[0],
+                     "spearman_cost_vs_time": spearman,
+                     "sets_for_pick_schedule": len(same),
+                     "best_set_vs_mean_set_for_pick": (float(np.mean(same)) / min(same)) if same else None})
+    return {"metric": "performance-model accuracy", "graph": graph_name, "rows": rows}
 
 
 def reference_arm(a):
@@ -517,6 +623,12 @@ def main():
             print(json.dumps(reference_arm(a)), flush=True)
         return
     import torch
+    if a.mode == "model":
+        if rank == 0:
+            from paper_2009_10955_gb300 import native
+            out = model_bench(native(), torch.cuda.current_stream(), a.model_graph, a.model_patterns.split(","))
+            print(json.dumps(out), flush=True)
+        return
     if a.mode == "serve":
         if rank == 0:
             from paper_2009_10955_gb300 import native

@@ -195,9 +195,11 @@ typedef struct gp_count_opts {
     int32_t warps_per_block;  /* 1..32                                               */
     int32_t blocks_per_sm;    /* resident blocks per SM for the persistent grid       */
     int32_t chunk;            /* edge tasks claimed per work-queue grab               */
-    int32_t split;            /* second-level split: an edge task whose level-2
-                                 candidate list is longer than this is cut into
-                                 pieces of this many candidates (0 = default)        */
+    int32_t split;            /* second-level split: every edge task whose first
+                                 vertex has degree >= 256 is cut into this many
+                                 parts that share out its depth-2 candidates, each
+                                 handed to whichever warp is free (0/1 = no split;
+                                 ignored with a budget and for 3-vertex patterns)   */
     int32_t flags;            /* GP_COUNT_STATS                                      */
     int64_t task_begin;       /* first edge task (CSR entry) to process              */
     int64_t task_end;         /* one past the last (0 = all)                         */
@@ -214,6 +216,12 @@ typedef struct gp_count_opts {
     int32_t lane_work;        /* probe/merge steps above which a lane hands its
                                  last-level count to the whole warp (0 = 192)        */
     int32_t reserved1;
+    int64_t task_cycles;      /* per-work-item clock64 limit, checked inside the
+                                 search loops (0 = none). A job whose work item
+                                 outlives it is abandoned: gp_count and
+                                 gp_count_batch return GP_ERR_TIMEOUT,
+                                 gp_count_batch_ranges sets its next_task to -1.
+                                 Other jobs of the same launch are unaffected.    */
 } gp_count_opts;
 
 /* gp_count_opts.flags */
@@ -242,8 +250,9 @@ gp_status gp_count_batch(gp_graph* const* graphs, const gp_schedules* const* sch
  * opts->budget_cycles may stop the launch early. Work items are handed out
  * in job order, so a stopped launch leaves every job with a processed
  * prefix: out[j] receives the count over that prefix and next_task[j] the
- * first unprocessed task (== the job's end when it is complete). Returns
- * GP_OK when every job completed, GP_PARTIAL otherwise; counts over disjoint
+ * first unprocessed task (== the job's end when it is complete; -1 when the
+ * job was abandoned under opts->task_cycles). Returns GP_OK when every job
+ * completed, GP_PARTIAL otherwise; counts over disjoint
  * task ranges add up to the full count. Synchronises `stream`. This is the
  * call a continuous-batching server issues once per time slice. */
 gp_status gp_count_batch_ranges(gp_graph* const* graphs, const gp_schedules* const* scheds,

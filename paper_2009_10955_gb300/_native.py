@@ -79,6 +79,7 @@ class gp_count_opts(ctypes.Structure):
         ("algo_bytes", ctypes.POINTER(ctypes.c_uint64)),
         ("lane_work", ctypes.c_int32),
         ("reserved1", ctypes.c_int32),
+        ("task_cycles", ctypes.c_int64),
     ]
 
 

@@ -9,7 +9,9 @@ Knobs (all fields of ``gp_count_opts``):
   warp-cooperative intersection);
 * ``GP_COUNT_NO_CORE`` -- whether intersections may use the core bit matrix
   (bit probes) or always binary-search (the intersection variant);
-* ``chunk`` -- edge tasks per work-queue grab outside the high-degree prefix.
+* ``chunk`` -- edge tasks per work-queue grab outside the high-degree prefix;
+* ``split`` -- parts each high-degree-prefix task is cut into (the
+  second-level split depth of the work decomposition).
 
 A configuration is timed (CUDA events around the kernel, inside the library)
 on a stratified sample of the edge tasks: ``windows`` evenly spaced windows
@@ -30,6 +32,7 @@ DEFAULT_SPACE = {
     "lane_work": [64, 192, 512],
     "core": [True, False],
     "chunk": [0, 4],
+    "split": [1, 8],
 }
 
 
@@ -43,7 +46,8 @@ def _key(graph, sched, idx, device):
 def opts_for(cfg, **extra):
     flags = 0 if cfg.get("core", True) else N.GP_COUNT_NO_CORE
     return N.make_opts(blocks_per_sm=cfg["blocks_per_sm"], lane_work=cfg["lane_work"],
-                       chunk=cfg["chunk"], flags=flags | extra.pop("flags", 0), **extra)
+                       chunk=cfg["chunk"], split=cfg.get("split", 1), flags=flags | extra.pop("flags", 0),
+                       **extra)
 
 
 def sample_ranges(nnz, windows, width):

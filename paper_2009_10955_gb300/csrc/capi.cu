@@ -88,6 +88,8 @@ gp_status triangle_count(gp_graph* g, cudaStream_t st, uint64_t* out) {
     job.ntasks = g->nnz;
     job.task_offset = 0;
     job.heavy = 0;                              // three-vertex plan: full chunks
+    job.split = 1;
+    job.nvirt = job.ntasks;
     job.core_bits = g->core_bits;
     job.core_n = g->core_n;
     job.core_words = g->core_words;
@@ -122,6 +124,12 @@ gp_status make_job(gp_graph* g, const gp_schedules* s, int32_t idx, const gp_cou
     // single-task grabs only pay off where a task runs loops of its own; a
     // three-vertex plan handles one task per lane and wants full chunks
     job->heavy = job->plan.k == 3 ? 0 : std::min<int64_t>(std::max<int64_t>(g->heavy_end - b, 0), e - b);
+    // parts per heavy task: only for counts that run to completion (a stop
+    // inside a split task could not be resumed exactly)
+    job->split = 1;
+    if (opts && opts->split > 1 && opts->budget_cycles <= 0 && job->plan.k > 3)
+        job->split = std::min(opts->split, 1024);
+    job->nvirt = job->heavy * job->split + (job->ntasks - job->heavy);
     job->core_bits = g->core_bits;
     job->core_n = g->core_n;
     job->core_words = g->core_words;
@@ -161,6 +169,7 @@ LaunchOpts launch_opts(const gp_count_opts* o) {
         if (o->budget_cycles > 0) lo.budget_cycles = o->budget_cycles;
         lo.stats = (o->flags & GP_COUNT_STATS) != 0;
         lo.no_core = (o->flags & GP_COUNT_NO_CORE) != 0;
+        if (o->task_cycles > 0) lo.task_cycles = o->task_cycles;
         if (o->lane_work > 0) lo.lane_work = o->lane_work;
     }
     return lo;
@@ -516,15 +525,17 @@ gp_status gp_count(gp_graph* g, const gp_schedules* s, int32_t idx, const gp_cou
     float ms = 0.f;
     uint64_t bytes = 0;
     const bool want_ms = opts && opts->kernel_ms;
+    int aborted = 0;
     rc = run_count(&job, 1, launch_opts(opts), static_cast<cudaStream_t>(stream), res, &done,
-                   want_ms ? &ms : nullptr, &bytes);
+                   want_ms ? &ms : nullptr, &bytes, &aborted);
     if (rc != GP_OK) return rc;
+    if (aborted) return fail(GP_ERR_TIMEOUT, "a work item outlived opts.task_cycles; the count was abandoned");
     uint64_t total = 0;
     rc = finish_total(job.plan, res[0], res[1], &total);
     if (rc != GP_OK) return rc;
     if (want_ms) *opts->kernel_ms = ms;
     if (opts && opts->algo_bytes && (opts->flags & GP_COUNT_STATS)) *opts->algo_bytes = bytes;
-    if (done < job.ntasks) {
+    if (done < job.nvirt) {
         if (opts && opts->resume_cursor) *opts->resume_cursor = job.task_begin + done;
         *out = total;
         return GP_PARTIAL;
@@ -543,11 +554,15 @@ gp_status gp_count_batch(gp_graph* const* graphs, const gp_schedules* const* sch
     std::vector<CountJob> jobs((size_t)njobs);
     int64_t off = 0;
     for (int32_t j = 0; j < njobs; ++j) {
-        gp_status rc = make_job(graphs[j], scheds[j], idx ? idx[j] : 0, nullptr, &jobs[j]);
+        gp_count_opts r;
+        std::memset(&r, 0, sizeof(r));
+        r.struct_size = sizeof(r);
+        r.split = opts ? opts->split : 0;
+        gp_status rc = make_job(graphs[j], scheds[j], idx ? idx[j] : 0, &r, &jobs[j]);
         if (rc != GP_OK) return rc;
         if (graphs[j]->device != graphs[0]->device) return fail(GP_ERR_ARG, "graphs on different devices");
         jobs[j].task_offset = off;
-        off += jobs[j].ntasks;
+        off += jobs[j].nvirt;
     }
     gp_status rc = ensure_device(graphs[0]);
     if (rc != GP_OK) return rc;
@@ -558,9 +573,12 @@ gp_status gp_count_batch(gp_graph* const* graphs, const gp_schedules* const* sch
     float ms = 0.f;
     uint64_t bytes = 0;
     const bool want_ms = opts && opts->kernel_ms;
+    std::vector<int> aborted((size_t)njobs, 0);
     rc = run_count(jobs.data(), njobs, lo, static_cast<cudaStream_t>(stream), res.data(), &done,
-                   want_ms ? &ms : nullptr, &bytes);
+                   want_ms ? &ms : nullptr, &bytes, aborted.data());
     if (rc != GP_OK) return rc;
+    for (int32_t j = 0; j < njobs; ++j)
+        if (aborted[j]) return fail(GP_ERR_TIMEOUT, "a work item outlived opts.task_cycles; the batch was abandoned");
     if (want_ms) *opts->kernel_ms = ms;
     if (opts && opts->algo_bytes && (opts->flags & GP_COUNT_STATS)) *opts->algo_bytes = bytes;
     std::vector<uint64_t> tot((size_t)njobs);
@@ -587,12 +605,13 @@ gp_status gp_count_batch_ranges(gp_graph* const* graphs, const gp_schedules* con
         r.struct_size = sizeof(r);
         r.task_begin = task_begin ? task_begin[j] : 0;
         r.task_end = task_end ? task_end[j] : 0;
+        r.split = (opts && opts->budget_cycles <= 0) ? opts->split : 0;   // whole ranges only
         gp_status rc = make_job(graphs[j], scheds[j], idx ? idx[j] : 0, &r, &jobs[j]);
         if (rc != GP_OK) return rc;
         if (jobs[j].plan.iep) return fail(GP_ERR_ARG, "inclusion-exclusion plans count whole graphs only");
         if (graphs[j]->device != graphs[0]->device) return fail(GP_ERR_ARG, "graphs on different devices");
         jobs[j].task_offset = off;
-        off += jobs[j].ntasks;
+        off += jobs[j].nvirt;
     }
     gp_status rc = ensure_device(graphs[0]);
     if (rc != GP_OK) return rc;
@@ -600,17 +619,18 @@ gp_status gp_count_batch_ranges(gp_graph* const* graphs, const gp_schedules* con
     int64_t done = 0;
     float ms = 0.f;
     const bool want_ms = opts && opts->kernel_ms;
+    std::vector<int> aborted((size_t)njobs, 0);
     rc = run_count(jobs.data(), njobs, launch_opts(opts), static_cast<cudaStream_t>(stream), res.data(),
-                   &done, want_ms ? &ms : nullptr, nullptr);
+                   &done, want_ms ? &ms : nullptr, nullptr, aborted.data());
     if (rc != GP_OK) return rc;
     for (int32_t j = 0; j < njobs; ++j)
-        if (res[2 * j + 1]) return fail(GP_ERR_OVERFLOW, "a count does not fit in 64 bits");
+        if (res[2 * j + 1] && !aborted[j]) return fail(GP_ERR_OVERFLOW, "a count does not fit in 64 bits");
     bool all = true;
     for (int32_t j = 0; j < njobs; ++j) {
         int64_t p = std::min(std::max<int64_t>(done - jobs[j].task_offset, 0), jobs[j].ntasks);
-        out[j] = res[2 * j];
-        next_task[j] = jobs[j].task_begin + p;
-        all = all && p == jobs[j].ntasks;
+        out[j] = aborted[j] ? 0 : res[2 * j];
+        next_task[j] = aborted[j] ? -1 : jobs[j].task_begin + p;
+        all = all && !aborted[j] && p == jobs[j].ntasks;
     }
     if (want_ms) *opts->kernel_ms = ms;
     return all ? GP_OK : GP_PARTIAL;

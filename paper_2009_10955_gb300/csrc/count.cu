@@ -108,7 +108,20 @@ struct TaskCtx {
     int lane_work;         // per-lane work limit before handing to the warp
     int* err;
     unsigned long long* sbytes;   // algorithmic-byte tally (instrumented kernel only)
+    long long* deadline;   // this warp's current work-item deadline (shared memory; 0 = none)
+    long long task_cycles; // work-item cycle limit (0 = none)
+    int* job_abort;        // abort flag of the current job (global memory)
 };
+
+// True (on every lane) once the current work item has outlived its cycle
+// limit; the job is then marked abandoned. Call from warp-uniform code only.
+__device__ __forceinline__ bool over(const TaskCtx& c) {
+    const long long dl = *c.deadline;
+    if (dl == 0) return false;
+    const bool late = __any_sync(kFull, clock64() > dl);
+    if (late && c.lane == 0) atomicExch(c.job_abort, 1);
+    return late;
+}
 
 // A sorted list: [p, p + n). v >= 0 when it is (a window of) N(v).
 struct List {
@@ -407,6 +420,7 @@ __device__ __forceinline__ void lane_parallel_last_two(const TaskCtx& c, int* v,
     const int d = P.k - 2;
     const uint8_t ex = P.lvl[d].excl_mask;
     for (int base = 0; base < lst.n; base += 32) {
+        if (over(c)) return;
         const int i = base + c.lane;
         int x = -1;
         bool active = i < lst.n;
@@ -458,23 +472,36 @@ __device__ __forceinline__ uint32_t operand_word(const TaskCtx& c, const int* v,
 }
 
 // S_d = AND of the rows of its operands, inside its window, without the
-// already-matched vertices that may lie in it.
-__device__ __forceinline__ void bitmap_build(const TaskCtx& c, const int* v, int d, int W, bool n0_smem) {
+// already-matched vertices that may lie in it. Returns the number of words
+// that can hold its bits (its window ends before that). With bm_inc the set
+// is S_{d-1} AND the row of v_{d-1}.
+__device__ __forceinline__ int bitmap_build(const TaskCtx& c, const int* v, int d, int W, int Wprev,
+                                            bool n0_smem) {
     const GpLevel& L = c.P->lvl[d];
     const Window win = window(L.lo_mask, L.hi_mask, v);
+    const int Wd = min(W, (win.hi == INT_MAX) ? W : ((win.hi + 31) >> 5));
     uint32_t* S = c.bm + (size_t)d * c.bm_stride;
-    for (int w = c.lane; w < W; w += 32) {
-        uint32_t x = window_bits(w, win.lo, win.hi);
-        for (int j = 0; j < d && x; ++j)
-            if (L.op_mask >> j & 1) x &= operand_word(c, v, j, w, n0_smem);
-        S[w] = x;
+    if (L.bm_inc && d >= 3) {
+        const uint32_t* prev = c.bm + (size_t)(d - 1) * c.bm_stride;
+        const uint32_t* row = c.core_bits + (size_t)v[d - 1] * c.core_words;
+        const int Wi = min(Wd, Wprev);
+        for (int w = c.lane; w < Wd; w += 32)
+            S[w] = (w < Wi) ? (prev[w] & __ldg(row + w) & window_bits(w, win.lo, win.hi)) : 0u;
+    } else {
+        for (int w = c.lane; w < Wd; w += 32) {
+            uint32_t x = window_bits(w, win.lo, win.hi);
+            for (int j = 0; j < d && x; ++j)
+                if (L.op_mask >> j & 1) x &= operand_word(c, v, j, w, n0_smem);
+            S[w] = x;
+        }
     }
     __syncwarp();
     if (c.lane == 0)
         for (int j = 0; j < d; ++j)
-            if ((L.excl_mask >> j & 1) && v[j] > win.lo && v[j] < win.hi && v[j] < 32 * W)
+            if ((L.excl_mask >> j & 1) && v[j] > win.lo && v[j] < win.hi && v[j] < 32 * Wd)
                 S[v[j] >> 5] &= ~(1u << (v[j] & 31));
     __syncwarp();
+    return Wd;
 }
 
 // Next set bit of S_d at or after the iteration state (word, remaining bits).
@@ -488,32 +515,47 @@ __device__ __forceinline__ int bitmap_next(const uint32_t* S, int W, int& word, 
     return 32 * word + b;
 }
 
-// Every candidate x of depth k-2 (set S_{k-2}): add the size of the last
-// level's set, the AND of its operand rows in its window (which may depend
-// on x), minus matched vertices inside it.
-__device__ __forceinline__ void bitmap_last_two(const TaskCtx& c, int* v, int W, bool n0_smem, Acc& acc) {
+// Every candidate x of depth k-2 (set S_{k-2}, Wd words): add the size of
+// the last level's set, the AND of its operand rows in its window (which may
+// depend on x), minus matched vertices inside it. With bm_inc on the last
+// level that set is S_{k-2} AND the row of x.
+__device__ __forceinline__ void bitmap_last_two(const TaskCtx& c, int* v, int Wd, bool n0_smem, Acc& acc,
+                                                int part, int nparts) {
     const GpPlan& P = *c.P;
     const int d = P.k - 2, L = P.k - 1;
     const GpLevel& lv = P.lvl[L];
     const bool uses_x = lv.op_mask >> d & 1;
-    uint32_t* PP = c.bm + (size_t)1 * c.bm_stride;      // operands other than x
-    for (int w = c.lane; w < W; w += 32) {
-        uint32_t m = 0xffffffffu;
-        for (int j = 0; j < d && m; ++j)
-            if (lv.op_mask >> j & 1) m &= operand_word(c, v, j, w, n0_smem);
-        PP[w] = m;
-    }
-    __syncwarp();
     const uint32_t* S = c.bm + (size_t)d * c.bm_stride;
+    const uint32_t* PP = S;
+    if (!(lv.bm_inc && d >= 2)) {
+        uint32_t* pp = c.bm + (size_t)1 * c.bm_stride;   // operands other than x
+        for (int w = c.lane; w < Wd; w += 32) {
+            uint32_t m = 0xffffffffu;
+            for (int j = 0; j < d && m; ++j)
+                if (lv.op_mask >> j & 1) m &= operand_word(c, v, j, w, n0_smem);
+            pp[w] = m;
+        }
+        __syncwarp();
+        PP = pp;
+    }
+    // the window's part that does not depend on x, and whether x bounds it
+    const uint8_t xbit = (uint8_t)(1u << d);
+    const Window base = window(lv.lo_mask & (uint8_t)~xbit, lv.hi_mask & (uint8_t)~xbit, v);
+    const bool x_lo = lv.lo_mask & xbit, x_hi = lv.hi_mask & xbit;
+    const bool any_excl = (lv.excl_mask & (uint8_t)((2u << d) - 1)) != 0;
     int word = -1;
     uint32_t bits = 0;
+    int ordinal = 0;
     for (;;) {
-        const int x = bitmap_next(S, W, word, bits);
-        if (x < 0) break;
+        const int x = bitmap_next(S, Wd, word, bits);
+        if (x < 0 || over(c)) break;
+        if (d == 2 && (ordinal++ % nparts) != part) continue;   // another part's candidate
         v[d] = x;
-        const Window win = window(lv.lo_mask, lv.hi_mask, v);
+        Window win = base;
+        if (x_lo) win.lo = max(win.lo, x);
+        if (x_hi) win.hi = min(win.hi, x);
         const int w0 = max(0, (win.lo + 1) >> 5);
-        const int w1 = min(W, (win.hi == INT_MAX) ? W : ((win.hi + 31) >> 5));
+        const int w1 = min(Wd, (win.hi == INT_MAX) ? Wd : ((win.hi + 31) >> 5));
         const uint32_t* rx = c.core_bits + (size_t)x * c.core_words;
         unsigned long long cnt = 0;
         for (int w = w0 + c.lane; w < w1; w += 32) {
@@ -522,12 +564,12 @@ __device__ __forceinline__ void bitmap_last_two(const TaskCtx& c, int* v, int W,
             cnt += __popc(m);
         }
         acc.add(cnt);
-        if (c.lane == 0) {
+        if (any_excl && c.lane == 0) {
             int hits = 0;
             for (int j = 0; j <= d; ++j) {
                 if (!(lv.excl_mask >> j & 1)) continue;
                 const int y = v[j];
-                if (y <= win.lo || y >= win.hi || y >= 32 * W) continue;
+                if (y <= win.lo || y >= win.hi || y >= 32 * Wd) continue;
                 bool in = (PP[y >> 5] >> (y & 31)) & 1u;
                 if (in && uses_x) in = (__ldg(rx + (y >> 5)) >> (y & 31)) & 1u;
                 hits += in;
@@ -537,7 +579,7 @@ __device__ __forceinline__ void bitmap_last_two(const TaskCtx& c, int* v, int W,
     }
 }
 
-__device__ void bitmap_task(const TaskCtx& c, int* v, Acc& acc) {
+__device__ void bitmap_task(const TaskCtx& c, int* v, Acc& acc, int part, int nparts) {
     const GpPlan& P = *c.P;
     const int k = P.k;
     const int W = (v[1] + 31) >> 5;          // every later candidate is below v1
@@ -554,23 +596,25 @@ __device__ void bitmap_task(const TaskCtx& c, int* v, Acc& acc) {
         __syncwarp();
     }
     if (k == 4) {
-        bitmap_build(c, v, 2, W, n0_smem);
-        bitmap_last_two(c, v, W, n0_smem, acc);
+        const int W2 = bitmap_build(c, v, 2, W, W, n0_smem);
+        bitmap_last_two(c, v, W2, n0_smem, acc, part, nparts);
         return;
     }
-    int word[GP_MAX_K];
+    int word[GP_MAX_K], Wd[GP_MAX_K];
     uint32_t bits[GP_MAX_K];
-    int d = 2;
-    bitmap_build(c, v, 2, W, n0_smem);
+    int d = 2, ordinal2 = 0;
+    Wd[2] = bitmap_build(c, v, 2, W, W, n0_smem);
     word[2] = -1;
     bits[2] = 0;
     while (d >= 2) {
-        const int x = bitmap_next(c.bm + (size_t)d * c.bm_stride, W, word[d], bits[d]);
+        if (over(c)) return;
+        const int x = bitmap_next(c.bm + (size_t)d * c.bm_stride, Wd[d], word[d], bits[d]);
         if (x < 0) { --d; continue; }
+        if (d == 2 && (ordinal2++ % nparts) != part) continue;  // another part's candidate
         v[d] = x;
-        bitmap_build(c, v, d + 1, W, n0_smem);
+        Wd[d + 1] = bitmap_build(c, v, d + 1, W, Wd[d], n0_smem);
         if (d + 1 == k - 2) {
-            bitmap_last_two(c, v, W, n0_smem, acc);
+            bitmap_last_two(c, v, Wd[d + 1], n0_smem, acc, 0, 1);
         } else {
             ++d;
             word[d] = -1;
@@ -579,10 +623,17 @@ __device__ void bitmap_task(const TaskCtx& c, int* v, Acc& acc) {
     }
 }
 
-// Remaining loops of one edge task (v0, v1).
-__device__ void run_task(const TaskCtx& c, int v0, int v1, Acc& acc) {
+// Remaining loops of one edge task (v0, v1), or of part `part` of `nparts`
+// of it: the parts share out the candidates of depth 2.
+__device__ void run_task(const TaskCtx& c, int v0, int v1, Acc& acc, int part, int nparts) {
     const GpPlan& P = *c.P;
     const int k = P.k;
+    if (c.task_cycles > 0) {                 // work-item cycle limit
+        if (*(volatile int*)c.job_abort) return;
+        const long long now = __shfl_sync(kFull, clock64(), 0);
+        if (c.lane == 0) *c.deadline = now + c.task_cycles;
+        __syncwarp();
+    }
     int v[GP_MAX_K];
     List lst[GP_MAX_K];
     int cur[GP_MAX_K];
@@ -590,10 +641,15 @@ __device__ void run_task(const TaskCtx& c, int v0, int v1, Acc& acc) {
     for (int i = 0; i < GP_MAX_K; ++i) v[i] = -1;
     v[0] = v0;
     v[1] = v1;
-    if (P.core_dfs && c.bm && v1 < c.core_n) { bitmap_task(c, v, acc); return; }
+    if (P.core_dfs && c.bm && v1 < c.core_n) { bitmap_task(c, v, acc, part, nparts); return; }
+    if (k == 3 || (P.iep && k == 4)) {
+        if (part != 0) return;                 // no depth-2 loop to share out
+        run_builds(c, 1, v);
+        if (k == 3) count_last(c, v, acc);
+        else iep_count(c, v, acc);
+        return;
+    }
     run_builds(c, 1, v);
-    if (k == 3) { count_last(c, v, acc); return; }
-    if (P.iep && k == 4) { iep_count(c, v, acc); return; }
     auto prepare = [&](int dd) {
         const GpLevel& L = P.lvl[dd];
         lst[dd] = clip((L.src_kind == 1) ? nbr(c, v[L.src]) : slot(c, L.src), window(L.lo_mask, L.hi_mask, v));
@@ -602,6 +658,12 @@ __device__ void run_task(const TaskCtx& c, int v0, int v1, Acc& acc) {
     const bool lane_last = P.lvl[k - 2].nbuild == 0;
     int d = 2;
     prepare(2);
+    if (nparts > 1) {                          // this part's share of depth 2
+        const int n = lst[2].n;
+        const int b = (int)((int64_t)n * part / nparts), e = (int)((int64_t)n * (part + 1) / nparts);
+        lst[2].p += b;
+        lst[2].n = e - b;
+    }
     while (d >= 2) {
         if (lane_last && d == k - 2) {
             lane_parallel_last_two(c, v, lst[d], acc);
@@ -609,6 +671,7 @@ __device__ void run_task(const TaskCtx& c, int v0, int v1, Acc& acc) {
             continue;
         }
         if (cur[d] >= lst[d].n) { --d; continue; }
+        if (over(c)) return;
         const int x = __ldg(lst[d].p + cur[d]);
         ++cur[d];
         if (c.sbytes && c.lane == 0) *c.sbytes += 4;
@@ -630,11 +693,12 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
         unsigned long long* __restrict__ cursor, unsigned long long* __restrict__ results,
         int32_t* __restrict__ slot_pool, int64_t warp_elems, int chunk, long long budget,
         int* __restrict__ err, unsigned long long* __restrict__ stats, int lane_work, int use_core,
-        int bm_stride, int bm_sets) {
+        int bm_stride, int bm_sets, long long task_cycles, int* __restrict__ aborts) {
     unsigned long long my_bytes = 0;
     extern __shared__ uint32_t s_bitmaps[];   // bm_sets x bm_stride words per warp (may be empty)
     __shared__ GpPlan s_plan[kWarps];
     __shared__ int s_len[kWarps][GP_MAX_SLOTS];
+    __shared__ long long s_deadline[kWarps];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t gw = (int64_t)blockIdx.x * kWarps + w;
     TaskCtx c;
@@ -645,6 +709,11 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
     c.bm = (bm_stride > 0 && !kStats) ? s_bitmaps + (size_t)w * bm_sets * bm_stride : nullptr;
     c.lane = lane;
     c.lane_work = lane_work;
+    c.deadline = &s_deadline[w];
+    c.task_cycles = task_cycles;
+    c.job_abort = aborts;
+    if (lane == 0) s_deadline[w] = 0;
+    __syncwarp();
     c.err = err;
     c.row_ptr = nullptr;
     c.col = nullptr;
@@ -655,7 +724,8 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
     c.n_vertices = 0;
     c.sbytes = kStats ? &my_bytes : nullptr;
     int cur_job = -1;
-    int64_t job_lo = 0, job_hi = 0, job_begin = 0;
+    int64_t job_lo = 0, job_hi = 0, job_begin = 0, job_heavy = 0;
+    int job_split = 1;
     Acc acc;
     const long long t_start = clock64();
     for (;;) {
@@ -672,7 +742,7 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
                     int mid = (lo + hi + 1) >> 1;
                     if (jobs[mid].task_offset <= peek) lo = mid; else hi = mid - 1;
                 }
-                if (peek - jobs[lo].task_offset < jobs[lo].heavy) grab = 1;
+                if (peek - jobs[lo].task_offset < jobs[lo].heavy * jobs[lo].split) grab = 1;
             }
             t0 = atomicAdd(cursor, (unsigned long long)grab);
         }
@@ -690,14 +760,17 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
                 }
                 if (cur_job >= 0) flush(acc, results + 2 * cur_job);
                 cur_job = lo;
+                c.job_abort = aborts + lo;
                 const CountJob& J = jobs[lo];
                 const int* src = reinterpret_cast<const int*>(&J.plan);
                 int* dst = reinterpret_cast<int*>(&s_plan[w]);
                 for (int i = lane; i < (int)(sizeof(GpPlan) / 4); i += 32) dst[i] = src[i];
                 __syncwarp();
                 job_lo = J.task_offset;
-                job_hi = J.task_offset + J.ntasks;
+                job_hi = J.task_offset + J.nvirt;
                 job_begin = J.task_begin;
+                job_heavy = J.heavy;
+                job_split = J.split > 0 ? J.split : 1;
                 c.row_ptr = J.row_ptr;
                 c.col = J.col;
                 c.core_bits = J.core_bits;
@@ -711,8 +784,27 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
                 c.n_vertices = J.n;
             }
             const int64_t tend = min(t1, job_hi);
-            int64_t e = job_begin + (t - job_lo);
-            const int64_t e_end = job_begin + (tend - job_lo);
+            // work items of the split high-degree prefix: (task, part)
+            const int64_t hp = job_heavy * job_split;
+            int64_t lt = t - job_lo;
+            const int64_t lt_end = tend - job_lo;
+            const uint8_t lo1s = s_plan[w].lvl[1].lo_mask & 1, hi1s = s_plan[w].lvl[1].hi_mask & 1;
+            for (; lt < lt_end && lt < hp; ++lt) {
+                const int64_t eh = job_begin + lt / job_split;
+                const int part = (int)(lt % job_split);
+                int rl = 0, rh = c.n_vertices - 1;
+                while (rl < rh) {
+                    int mid = (rl + rh + 1) >> 1;
+                    if (__ldg(c.row_ptr + mid) <= eh) rl = mid; else rh = mid - 1;
+                }
+                const int hv1 = __ldg(c.col + eh);
+                if (lo1s && !(hv1 > rl)) continue;
+                if (hi1s && !(hv1 < rl)) continue;
+                run_task(c, rl, hv1, acc, part, job_split);
+            }
+            if (lt >= lt_end) { t = tend; continue; }
+            int64_t e = job_begin + job_heavy + (lt - hp);
+            const int64_t e_end = job_begin + job_heavy + (lt_end - hp);
             // source vertex of entry e: last u with row_ptr[u] <= e
             int lo = 0, hi = c.n_vertices - 1;
             while (lo < hi) {
@@ -763,7 +855,7 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
                     const int v1 = __ldg(c.col + e);
                     if (lo1 && !(v1 > v0)) continue;
                     if (hi1 && !(v1 < v0)) continue;
-                    run_task(c, v0, v1, acc);
+                    run_task(c, v0, v1, acc, 0, 1);
                 }
             }
             t = tend;
@@ -781,7 +873,8 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
 namespace {
 
 using KernelFn = void (*)(const CountJob*, int, int64_t, unsigned long long*, unsigned long long*,
-                          int32_t*, int64_t, int, long long, int*, unsigned long long*, int, int, int, int);
+                          int32_t*, int64_t, int, long long, int*, unsigned long long*, int, int, int, int,
+                          long long, int*);
 
 struct Geometry {
     KernelFn kern;
@@ -801,7 +894,7 @@ gp_status geometry(const CountJob* jobs, int njobs, const LaunchOpts& opt, Geome
     g->total = 0;
     g->warp_elems = 1;
     for (int j = 0; j < njobs; ++j) {
-        g->total += jobs[j].ntasks;
+        g->total += jobs[j].nvirt;
         g->warp_elems = std::max<int64_t>(g->warp_elems, (int64_t)jobs[j].plan.nslots * jobs[j].slot_cap);
     }
     int dev = 0, nsm = 0;
@@ -854,7 +947,8 @@ gp_status scratch_bytes(const CountJob* jobs, int njobs, const LaunchOpts& opt, 
 }
 
 gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& opt, cudaStream_t st,
-                    uint64_t* results, int64_t* processed, float* kernel_ms, uint64_t* algo_bytes) {
+                    uint64_t* results, int64_t* processed, float* kernel_ms, uint64_t* algo_bytes,
+                    int* aborted) {
     if (njobs <= 0) { set_error("no jobs"); return GP_ERR_ARG; }
     Geometry geo;
     gp_status grc = geometry(jobs, njobs, opt, &geo);
@@ -870,7 +964,8 @@ gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& opt, cuda
 
     // device buffers: job table, results (2 per job), cursor, error word
     const size_t jobs_b = sizeof(CountJob) * (size_t)njobs;
-    const size_t res_b = sizeof(unsigned long long) * (2 * (size_t)njobs + 3);
+    // results (2 per job), cursor, error word, stats, then one abort flag per job
+    const size_t res_b = sizeof(unsigned long long) * (2 * (size_t)njobs + 3) + sizeof(int) * (size_t)njobs;
     void* d_mem = nullptr;
     int32_t* d_slots = nullptr;
     GP_CUDA_TRY(cudaMallocAsync(&d_mem, jobs_b + res_b + 64, st));
@@ -885,8 +980,9 @@ gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& opt, cuda
     unsigned long long* d_cursor = d_res + 2 * njobs;
     int* d_err = reinterpret_cast<int*>(d_cursor + 1);
     unsigned long long* d_stats = d_cursor + 2;
+    int* d_aborts = reinterpret_cast<int*>(d_stats + 1);
     gp_status rc = GP_OK;
-    std::vector<unsigned long long> h_res(2 * (size_t)njobs + 3, 0);
+    std::vector<unsigned long long> h_res((res_b + 7) / 8, 0);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (kernel_ms) {
         GP_CUDA_TRY(cudaEventCreate(&ev0));
@@ -899,7 +995,8 @@ gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& opt, cuda
         kern<<<(unsigned)blocks, kWarps * 32, geo.smem, st>>>(d_jobs, njobs, total, d_cursor, d_res, d_slots,
                                                       warp_elems, chunk, (long long)opt.budget_cycles,
                                                       d_err, d_stats, opt.lane_work > 0 ? opt.lane_work : kLaneWork,
-                                                      opt.no_core ? 0 : 1, geo.bm_stride, geo.bm_sets);
+                                                      opt.no_core ? 0 : 1, geo.bm_stride, geo.bm_sets,
+                                                      (long long)opt.task_cycles, d_aborts);
         count_launch();
         e = cudaGetLastError();
     }
@@ -926,6 +1023,10 @@ gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& opt, cuda
     }
     for (int j = 0; j < 2 * njobs; ++j) results[j] = h_res[j];
     if (algo_bytes) *algo_bytes = h_res[2 * njobs + 2];
+    if (aborted) {
+        const int* flags = reinterpret_cast<const int*>(h_res.data() + 2 * njobs + 3);
+        for (int j = 0; j < njobs; ++j) aborted[j] = flags[j];
+    }
     int64_t done = (int64_t)std::min<unsigned long long>(h_res[2 * njobs], (unsigned long long)total);
     if (processed) *processed = total == 0 ? 0 : done;
     return rc;
@@ -936,7 +1037,7 @@ gp_status run_count_in_scratch(const CountJob* jobs, int njobs, void* d_scratch,
     constexpr int kMaxJobs = 8;            // host result words live on the stack
     if (njobs <= 0 || njobs > kMaxJobs) { set_error("1 to %d jobs per call", kMaxJobs); return GP_ERR_ARG; }
     // layout: [result words | job table | intermediate sets], 256-byte aligned
-    const size_t words_b = ((sizeof(unsigned long long) * (2 * (size_t)njobs + 3)) + 255) & ~(size_t)255;
+    const size_t words_b = ((sizeof(unsigned long long) * (2 * (size_t)njobs + 4)) + 255) & ~(size_t)255;
     const size_t jobs_b = ((sizeof(CountJob) * (size_t)njobs) + 255) & ~(size_t)255;
     if (words_b + jobs_b > scratch_bytes) {
         set_error("%d jobs need %zu bytes of fixed scratch for results and job table; it holds %zu",
@@ -945,7 +1046,7 @@ gp_status run_count_in_scratch(const CountJob* jobs, int njobs, void* d_scratch,
     }
     int64_t total = 0, warp_elems = 1;
     for (int j = 0; j < njobs; ++j) {
-        total += jobs[j].ntasks;
+        total += jobs[j].nvirt;
         warp_elems = std::max<int64_t>(warp_elems, (int64_t)jobs[j].plan.nslots * jobs[j].slot_cap);
     }
     const size_t per_block = (size_t)kWarps * (size_t)warp_elems * sizeof(int32_t);
@@ -968,6 +1069,7 @@ gp_status run_count_in_scratch(const CountJob* jobs, int njobs, void* d_scratch,
     unsigned long long* d_cursor = d_res + 2 * njobs;
     int* d_err = reinterpret_cast<int*>(d_cursor + 1);
     unsigned long long* d_stats = d_cursor + 2;
+    int* d_aborts = reinterpret_cast<int*>(d_stats + 1);       // unused: no cycle limit here
     CountJob* d_jobs = reinterpret_cast<CountJob*>(base + words_b);
     int32_t* d_slots = reinterpret_cast<int32_t*>(base + words_b + jobs_b);
     unsigned long long h_res[2 * kMaxJobs + 3] = {};
@@ -976,7 +1078,8 @@ gp_status run_count_in_scratch(const CountJob* jobs, int njobs, void* d_scratch,
     GP_CUDA_TRY(cudaMemsetAsync(d_res, 0, words_b, st));       // results, cursor, error word start at 0
     if (total > 0) {
         kern<<<(unsigned)blocks, kWarps * 32, 0, st>>>(d_jobs, njobs, total, d_cursor, d_res, d_slots,
-                                                      warp_elems, chunk, 0, d_err, d_stats, kLaneWork, 1, 0, 0);
+                                                      warp_elems, chunk, 0, d_err, d_stats, kLaneWork, 1, 0, 0,
+                                                      0, d_aborts);
         count_launch();
         GP_CUDA_TRY(cudaGetLastError());
     }

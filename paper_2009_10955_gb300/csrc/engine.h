@@ -59,8 +59,11 @@ struct CountJob {
     int32_t slot_cap;        // elements per intermediate set (>= max degree)
     int64_t task_begin;      // first CSR entry (edge task) of this job
     int64_t ntasks;          // edge tasks of this job
-    int64_t task_offset;     // first global task index of this job
+    int64_t task_offset;     // first global work-item index of this job
     int64_t heavy;           // leading tasks of this job handed out one at a time
+    int32_t split;           // parts each of those tasks is cut into (>= 1)
+    int32_t pad0;
+    int64_t nvirt;           // work items: heavy * split + (ntasks - heavy)
     const uint32_t* core_bits;  // core adjacency bit matrix (null: none)
     int32_t core_n;
     int32_t core_words;
@@ -81,6 +84,7 @@ struct LaunchOpts {
     int64_t budget_cycles = 0;
     bool stats = false;      // instrumented kernel that tallies algorithmic bytes
     bool no_core = false;    // binary searches only (no core bit matrix)
+    int64_t task_cycles = 0; // per-work-item cycle limit (0 = none)
     int lane_work = 0;       // 0 = default
 };
 
@@ -89,7 +93,7 @@ struct LaunchOpts {
 // global tasks (from 0) were completed (< total only with a budget).
 gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& lo, cudaStream_t st,
                     uint64_t* results, int64_t* processed, float* kernel_ms = nullptr,
-                    uint64_t* algo_bytes = nullptr);
+                    uint64_t* algo_bytes = nullptr, int* aborted = nullptr);
 
 // run_count without allocating: results, job table and intermediate sets all
 // live in the caller's device buffer d_scratch (256-byte aligned); the grid

@@ -34,7 +34,8 @@ struct GpLevel {
     uint8_t excl_mask; // earlier depths whose vertex may lie in the set (injectivity)
     int8_t nbuild;     // builds executed after v_d is bound
     uint8_t op_mask;   // depths whose neighbourhoods are intersected for this set
-    int8_t pad[1];
+    uint8_t bm_inc;    // set of depth d = set of depth d-1 ∩ N(v_{d-1}) (same
+                       // operands plus d-1, window no wider): built incrementally
     GpBuild build[GP_MAX_BUILDS];
 };
 

@@ -396,6 +396,12 @@ bool compile_plan(const PatternInfo& p, const int8_t* sched, ResMask res, GpPlan
         }
     }
     plan.nslots = nslots;
+    for (int x = 3; x < k; ++x) {
+        const GpLevel& A = plan.lvl[x - 1];
+        const GpLevel& B = plan.lvl[x];
+        plan.lvl[x].bm_inc = B.op_mask == (uint8_t)(A.op_mask | (1u << (x - 1))) &&
+                             (B.lo_mask & A.lo_mask) == A.lo_mask && (B.hi_mask & A.hi_mask) == A.hi_mask;
+    }
     plan.core_dfs = k >= 4;
     for (int x = 2; x < k; ++x)
         if (!gt[1][x]) plan.core_dfs = 0;      // some later vertex may exceed v_1

@@ -52,9 +52,13 @@ class Server:
     """Continuous batching over device-resident graphs (see module doc)."""
 
     def __init__(self, graphs, slice_ms=20.0, max_batch=256, mem_budget=None, stream=None,
-                 clock_ghz=1.9, max_slices=None):
+                 clock_ghz=1.9, max_slices=None, item_ms=None):
         self.graphs = dict(graphs)
         self.slice_cycles = int(slice_ms * 1e-3 * clock_ghz * 1e9)
+        # with item_ms, a single work item (edge task) that needs longer than
+        # that abandons its request with a timeout, so that a slice cannot
+        # outlive its budget by more than item_ms
+        self.item_cycles = int(item_ms * 1e-3 * clock_ghz * 1e9) if item_ms else 0
         self.max_batch = max_batch
         self.mem_budget = mem_budget
         self.stream = stream
@@ -127,7 +131,7 @@ class Server:
                 batch = list(self._active)
             if not batch:
                 continue
-            opts = N.make_opts(budget_cycles=self.slice_cycles)
+            opts = N.make_opts(budget_cycles=self.slice_cycles, task_cycles=self.item_cycles)
             try:
                 st, out, nxt = N.gp_count_batch_ranges(
                     [self.graphs[r.graph] for r in batch], [r.sched for r in batch],
@@ -146,9 +150,14 @@ class Server:
             with self._cv:
                 still = []
                 for r, c, t in zip(batch, out, nxt):
+                    r.slices += 1
+                    if int(t) < 0:                       # a work item outlived item_cycles
+                        r.error = TimeoutError(f"request {r.rid}: a work item exceeded the item limit")
+                        r.finish = now
+                        r.done.set()
+                        continue
                     r.acc += int(c)
                     r.next_task = int(t)
-                    r.slices += 1
                     if r.next_task >= r.end_task:
                         r.count, r.finish = r.acc, now
                         r.done.set()

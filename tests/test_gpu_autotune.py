@@ -36,8 +36,11 @@ def test_knobs_do_not_change_counts(env):
             for lane_work in (1, 64, 100000):
                 for flags in (0, N.GP_COUNT_NO_CORE):
                     for chunk in (0, 1, 7):
-                        o = N.make_opts(blocks_per_sm=bps, lane_work=lane_work, flags=flags, chunk=chunk)
-                        assert N.gp_count(g, sc, 0, o) == (N.GP_OK, expect), (pname, bps, lane_work, flags, chunk)
+                        for split in (1, 5):
+                            o = N.make_opts(blocks_per_sm=bps, lane_work=lane_work, flags=flags, chunk=chunk,
+                                            split=split)
+                            assert N.gp_count(g, sc, 0, o) == (N.GP_OK, expect), \
+                                (pname, bps, lane_work, flags, chunk, split)
 
 
 def test_tune_returns_and_caches(env, tmp_path):
@@ -47,7 +50,7 @@ def test_tune_returns_and_caches(env, tmp_path):
     adj = named_pattern("k4")
     sc = N.gp_schedule(N.gp_pattern_create(adj), g)
     cache = str(tmp_path / "tune.json")
-    space = {"blocks_per_sm": [2, 4], "lane_work": [64, 192], "core": [True, False], "chunk": [0]}
+    space = {"blocks_per_sm": [2, 4], "lane_work": [64, 192], "core": [True, False], "chunk": [0], "split": [1]}
     best, table = autotune.tune(g, sc, 0, space=space, windows=16, width=256, cache_path=cache)
     assert len(table) == 8 and best in [c for c, _ in table]
     best2, _ = autotune.tune(g, sc, 0, space=space, cache_path=cache)

@@ -174,6 +174,9 @@ def test_partial_core_graph(N, pname):
     got = N.gp_count(g, s)
     no_core = N.gp_count(g, s, 0, N.make_opts(flags=N.GP_COUNT_NO_CORE))
     assert got == no_core
+    for split in (2, 8, 33):           # high-degree tasks cut into parts
+        assert N.gp_count(g, s, 0, N.make_opts(split=split)) == got
+        assert N.gp_count(g, s, 0, N.make_opts(split=split, flags=N.GP_COUNT_NO_CORE)) == got
     if pname != "k5":
         assert got[1] == oracle.count_restricted(adj, order, res, ref)
     else:
@@ -181,6 +184,16 @@ def test_partial_core_graph(N, pname):
             o = N.make_opts(task_begin=int(ref.row_ptr[r]), task_end=int(ref.row_ptr[r + 1]))
             expect = oracle.count_restricted(adj, order, res, ref, root_begin=r, root_end=r + 1)
             assert N.gp_count(g, s, 0, o)[1] == expect, r
+
+
+@pytest.mark.parametrize("pname", ["house", "diamond", "c4"])
+def test_split_tasks_agree(N, pname):
+    g, ref = graph_pair(N, "rmat12")
+    s = N.gp_schedule(N.gp_pattern_create(named_pattern(pname)), g, top_k=2)
+    for i in range(len(s)):
+        base = N.gp_count(g, s, i)
+        for split in (3, 16):
+            assert N.gp_count(g, s, i, N.make_opts(split=split)) == base
 
 
 def test_degree_order_invariance(N):
