@@ -229,6 +229,9 @@ typedef struct gp_count_opts {
                               (slower; for measurement only)                      */
 #define GP_COUNT_NO_CORE 2 /* never use the core adjacency bit matrix: every
                               membership test is a binary search                  */
+#define GP_COUNT_WARP_BITMAP 4 /* bitmap subtree: count the last level one
+                              candidate at a time with the whole warp instead of
+                              one candidate per lane (for comparison)            */
 
 /* Count the embeddings of the pattern of `s` in `g` with plan `idx`.
  * Every embedding is counted exactly once (restrictions, Algorithm 1).

@@ -104,6 +104,7 @@ struct TaskCtx {
     int* slen;             // their lengths (shared memory, per warp)
     uint32_t* bm;          // this warp's bitmap sets (shared memory) or null
     int bm_stride;         // words per bitmap set
+    bool lane_bitmap;      // bitmap last level: one candidate per lane
     int lane;
     int lane_work;         // per-lane work limit before handing to the warp
     int* err;
@@ -519,15 +520,23 @@ __device__ __forceinline__ int bitmap_next(const uint32_t* S, int W, int& word, 
 // the last level's set, the AND of its operand rows in its window (which may
 // depend on x), minus matched vertices inside it. With bm_inc on the last
 // level that set is S_{k-2} AND the row of x.
-__device__ __forceinline__ void bitmap_last_two(const TaskCtx& c, int* v, int Wd, bool n0_smem, Acc& acc,
-                                                int part, int nparts) {
+__device__ __forceinline__ void bitmap_last_two(const TaskCtx& c, int* v, int W, int Ws, bool n0_smem,
+                                                Acc& acc, int part, int nparts) {
     const GpPlan& P = *c.P;
     const int d = P.k - 2, L = P.k - 1;
     const GpLevel& lv = P.lvl[L];
     const bool uses_x = lv.op_mask >> d & 1;
-    const uint32_t* S = c.bm + (size_t)d * c.bm_stride;
+    const uint32_t* S = c.bm + (size_t)d * c.bm_stride;      // candidates x (Ws words)
+    // the window's part that does not depend on x, and whether x bounds it
+    const uint8_t xbit = (uint8_t)(1u << d);
+    const Window base = window(lv.lo_mask & (uint8_t)~xbit, lv.hi_mask & (uint8_t)~xbit, v);
+    const bool x_lo = lv.lo_mask & xbit, x_hi = lv.hi_mask & xbit;
+    // words the last level's sets can use: its own window, which may be wider
+    // than S's unless the plan builds it from S (bm_inc)
     const uint32_t* PP = S;
+    int Wd = Ws;
     if (!(lv.bm_inc && d >= 2)) {
+        Wd = min(W, (base.hi == INT_MAX) ? W : ((base.hi + 31) >> 5));
         uint32_t* pp = c.bm + (size_t)1 * c.bm_stride;   // operands other than x
         for (int w = c.lane; w < Wd; w += 32) {
             uint32_t m = 0xffffffffu;
@@ -538,16 +547,62 @@ __device__ __forceinline__ void bitmap_last_two(const TaskCtx& c, int* v, int Wd
         __syncwarp();
         PP = pp;
     }
-    // the window's part that does not depend on x, and whether x bounds it
-    const uint8_t xbit = (uint8_t)(1u << d);
-    const Window base = window(lv.lo_mask & (uint8_t)~xbit, lv.hi_mask & (uint8_t)~xbit, v);
-    const bool x_lo = lv.lo_mask & xbit, x_hi = lv.hi_mask & xbit;
     const bool any_excl = (lv.excl_mask & (uint8_t)((2u << d) - 1)) != 0;
+    if (c.lane_bitmap) {
+        // one candidate per lane: lane b takes bit b of word w of S and scans
+        // its row with 16-byte loads over its window (rows and sets are
+        // padded to multiples of 4 words); for one word the windows end at
+        // almost the same place, so the lanes stay balanced
+        const uint4* PP4 = reinterpret_cast<const uint4*>(PP);
+        int ordinal_base = 0;
+        unsigned long long mine_cnt = 0;
+        for (int w = 0; w < Ws; ++w) {
+            const uint32_t bw = S[w];
+            if (!bw) continue;
+            if (over(c)) return;
+            const int x = 32 * w + c.lane;
+            bool mine = (bw >> c.lane) & 1u;
+            if (d == 2 && nparts > 1) {
+                mine = mine && ((ordinal_base + __popc(bw & lanemask_lt())) % nparts) == part;
+            }
+            ordinal_base += __popc(bw);
+            if (!mine) continue;
+            const int lo = x_lo ? max(base.lo, x) : base.lo;
+            const int hi = x_hi ? min(base.hi, x) : base.hi;
+            const int w0 = max(0, (lo + 1) >> 5);
+            const int w1 = min(Wd, (hi == INT_MAX) ? Wd : ((hi + 31) >> 5));
+            const uint4* rx4 = reinterpret_cast<const uint4*>(c.core_bits + (size_t)x * c.core_words);
+            unsigned long long cnt = 0;
+            for (int q = w0 >> 2; 4 * q < w1; ++q) {
+                const uint4 a = PP4[q];
+                const uint4 r = uses_x ? __ldg(rx4 + q) : make_uint4(~0u, ~0u, ~0u, ~0u);
+                const uint32_t aw[4] = {a.x & r.x, a.y & r.y, a.z & r.z, a.w & r.w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int ww = 4 * q + t;
+                    if (ww >= w0 && ww < w1) cnt += __popc(aw[t] & window_bits(ww, lo, hi));
+                }
+            }
+            if (any_excl) {
+                for (int j = 0; j <= d; ++j) {
+                    if (!(lv.excl_mask >> j & 1)) continue;
+                    const int y = (j == d) ? x : v[j];
+                    if (y <= lo || y >= hi || y >= 32 * Wd) continue;
+                    bool in = (PP[y >> 5] >> (y & 31)) & 1u;
+                    if (in && uses_x) in = (__ldg(c.core_bits + (size_t)x * c.core_words + (y >> 5)) >> (y & 31)) & 1u;
+                    cnt -= in;
+                }
+            }
+            mine_cnt += cnt;
+        }
+        acc.add(mine_cnt);
+        return;
+    }
     int word = -1;
     uint32_t bits = 0;
     int ordinal = 0;
     for (;;) {
-        const int x = bitmap_next(S, Wd, word, bits);
+        const int x = bitmap_next(S, Ws, word, bits);
         if (x < 0 || over(c)) break;
         if (d == 2 && (ordinal++ % nparts) != part) continue;   // another part's candidate
         v[d] = x;
@@ -597,7 +652,7 @@ __device__ void bitmap_task(const TaskCtx& c, int* v, Acc& acc, int part, int np
     }
     if (k == 4) {
         const int W2 = bitmap_build(c, v, 2, W, W, n0_smem);
-        bitmap_last_two(c, v, W2, n0_smem, acc, part, nparts);
+        bitmap_last_two(c, v, W, W2, n0_smem, acc, part, nparts);
         return;
     }
     int word[GP_MAX_K], Wd[GP_MAX_K];
@@ -614,7 +669,7 @@ __device__ void bitmap_task(const TaskCtx& c, int* v, Acc& acc, int part, int np
         v[d] = x;
         Wd[d + 1] = bitmap_build(c, v, d + 1, W, Wd[d], n0_smem);
         if (d + 1 == k - 2) {
-            bitmap_last_two(c, v, Wd[d + 1], n0_smem, acc, 0, 1);
+            bitmap_last_two(c, v, W, Wd[d + 1], n0_smem, acc, 0, 1);
         } else {
             ++d;
             word[d] = -1;
@@ -693,7 +748,7 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
         unsigned long long* __restrict__ cursor, unsigned long long* __restrict__ results,
         int32_t* __restrict__ slot_pool, int64_t warp_elems, int chunk, long long budget,
         int* __restrict__ err, unsigned long long* __restrict__ stats, int lane_work, int use_core,
-        int bm_stride, int bm_sets, long long task_cycles, int* __restrict__ aborts) {
+        int bm_stride, int bm_sets, long long task_cycles, int* __restrict__ aborts, int lane_bitmap) {
     unsigned long long my_bytes = 0;
     extern __shared__ uint32_t s_bitmaps[];   // bm_sets x bm_stride words per warp (may be empty)
     __shared__ GpPlan s_plan[kWarps];
@@ -710,6 +765,7 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
     c.lane = lane;
     c.lane_work = lane_work;
     c.deadline = &s_deadline[w];
+    c.lane_bitmap = lane_bitmap != 0;
     c.task_cycles = task_cycles;
     c.job_abort = aborts;
     if (lane == 0) s_deadline[w] = 0;
@@ -874,7 +930,7 @@ namespace {
 
 using KernelFn = void (*)(const CountJob*, int, int64_t, unsigned long long*, unsigned long long*,
                           int32_t*, int64_t, int, long long, int*, unsigned long long*, int, int, int, int,
-                          long long, int*);
+                          long long, int*, int);
 
 struct Geometry {
     KernelFn kern;
@@ -996,7 +1052,7 @@ gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& opt, cuda
                                                       warp_elems, chunk, (long long)opt.budget_cycles,
                                                       d_err, d_stats, opt.lane_work > 0 ? opt.lane_work : kLaneWork,
                                                       opt.no_core ? 0 : 1, geo.bm_stride, geo.bm_sets,
-                                                      (long long)opt.task_cycles, d_aborts);
+                                                      (long long)opt.task_cycles, d_aborts, opt.warp_bitmap ? 0 : 1);
         count_launch();
         e = cudaGetLastError();
     }
@@ -1079,7 +1135,7 @@ gp_status run_count_in_scratch(const CountJob* jobs, int njobs, void* d_scratch,
     if (total > 0) {
         kern<<<(unsigned)blocks, kWarps * 32, 0, st>>>(d_jobs, njobs, total, d_cursor, d_res, d_slots,
                                                       warp_elems, chunk, 0, d_err, d_stats, kLaneWork, 1, 0, 0,
-                                                      0, d_aborts);
+                                                      0, d_aborts, 1);
         count_launch();
         GP_CUDA_TRY(cudaGetLastError());
     }

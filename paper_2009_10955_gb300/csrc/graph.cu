@@ -200,7 +200,8 @@ __global__ void k_core_bits(const int64_t* __restrict__ row_ptr, const int32_t* 
 
 gp_status build_core_bits(gp_graph* g, int32_t core_n, cudaStream_t st) {
     if (core_n <= 0) return GP_OK;
-    const int32_t words = (core_n + 31) / 32;
+    // rows padded to a multiple of 4 words: 16-byte loads stay aligned
+    const int32_t words = (((core_n + 31) / 32) + 3) & ~3;
     const size_t bytes = sizeof(uint32_t) * (size_t)core_n * (size_t)words;
     uint32_t* bits = nullptr;
     GP_CUDA_TRY(cudaMalloc(&bits, bytes));

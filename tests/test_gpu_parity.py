@@ -133,6 +133,32 @@ def test_every_configuration_agrees(N, pname):
         assert N.gp_count(g, sc) == (N.GP_OK, expect), (s, r)
 
 
+@pytest.mark.parametrize("gname", ["er:300:1500:5", "rmat10"])
+@pytest.mark.parametrize("pname", ["c4", "c5", "house", "diamond", "tailed_triangle", "k4", "path4", "k5"])
+def test_bitmap_paths_equal_list_path(N, gname, pname):
+    """Every sampled configuration: the core bit-matrix paths (one candidate
+    per lane, and one per warp) give the count of the pure list path, which
+    equals the oracle's."""
+    g, ref = graph_pair(N, gname)
+    adj = named_pattern(pname)
+    p = N.gp_pattern_create(adj)
+    scheds, _ = p.schedules()
+    sets = p.restriction_sets()
+    pairs = [(sc, r) for sc in scheds for r in sets]
+    step = max(1, len(pairs) // 150)
+    expect = None
+    for sc, r in pairs[::step]:
+        one = N.gp_schedule_explicit(p, sc, r)
+        lists = N.gp_count(g, one, 0, N.make_opts(flags=N.GP_COUNT_NO_CORE))
+        assert N.gp_count(g, one) == lists, (sc, r)
+        assert N.gp_count(g, one, 0, N.make_opts(flags=N.GP_COUNT_WARP_BITMAP)) == lists, (sc, r)
+        if expect is None:
+            expect = lists
+        assert lists == expect, (sc, r)
+    if gname.startswith("er") or pname in ("c4", "k4", "diamond", "tailed_triangle", "path4"):
+        assert expect[1] == oracle.count(adj, ref)
+
+
 def test_random_patterns_batched_equals_single_and_oracle(N):
     g, ref = graph_pair(N, "er:300:1500:5")
     pats = random_pattern_set(16, 3, 6, 0.5, seed=11)
