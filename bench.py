@@ -513,8 +513,7 @@ def serve_bench(N, stream, scales, rates, per_rate, deadline_s, slice_ms, seed=7
     rows = []
     for ri, rate in enumerate(rates):
         arr = poisson_arrivals(rate, per_rate, seed + ri)
-        srv = Server(graphs, slice_ms=slice_ms, stream=stream, item_ms=20 * slice_ms,
-                     max_slices=max(1, int(deadline_s * 1000.0 / slice_ms)))
+        srv = Server(graphs, slice_ms=slice_ms, stream=stream, item_ms=20 * slice_ms, deadline_s=deadline_s)
         t0 = time.perf_counter()
         reqs = []
         for i, at in enumerate(arr):

@@ -229,9 +229,10 @@ typedef struct gp_count_opts {
                               (slower; for measurement only)                      */
 #define GP_COUNT_NO_CORE 2 /* never use the core adjacency bit matrix: every
                               membership test is a binary search                  */
-#define GP_COUNT_WARP_BITMAP 4 /* bitmap subtree: count the last level one
-                              candidate at a time with the whole warp instead of
-                              one candidate per lane (for comparison)            */
+#define GP_COUNT_WARP_BITMAP 4 /* bitmap subtree: always count the last level one
+                              candidate at a time with the whole warp (default:
+                              one candidate per lane for patterns of 5 or more
+                              vertices, the whole warp for 4)                    */
 
 /* Count the embeddings of the pattern of `s` in `g` with plan `idx`.
  * Every embedding is counted exactly once (restrictions, Algorithm 1).
@@ -268,6 +269,24 @@ gp_status gp_count_batch_ranges(gp_graph* const* graphs, const gp_schedules* con
  * intermediate sets with the given options (for admission control). */
 gp_status gp_count_scratch_bytes(const gp_graph* g, const gp_schedules* s, int32_t idx,
                                  const gp_count_opts* opts, uint64_t* bytes);
+
+/* Listing (the embeddings themselves, Section II-A: "find all distinct
+ * subgraphs"): the embeddings of plan idx whose edge tasks lie in
+ * [task_begin, task_end) (task_end <= 0: all), each written once as k
+ * int32 graph vertex ids, entry a being the image of pattern vertex a (ids
+ * of the graph's own labelling: with GP_DEGREE_ORDER map them back with
+ * gp_graph_copy_csr's perm). out is a device buffer of capacity embeddings
+ * (capacity * k int32, owned by the caller). Back-pressure: a call writes
+ * the embeddings of the longest prefix of the tasks that fits, in task
+ * order and, within a task, in search order (so repeated calls with the
+ * returned *next_task list every embedding exactly once, in the same order
+ * as one large call); *n_written receives how many were written. Returns
+ * GP_OK when the range is done, GP_PARTIAL when *next_task < task_end,
+ * GP_ERR_SCRATCH when the first task alone needs more than capacity.
+ * Inclusion-exclusion plans cannot list (GP_ERR_ARG). Synchronises. */
+gp_status gp_list(gp_graph* g, const gp_schedules* s, int32_t idx, int64_t task_begin,
+                  int64_t task_end, int32_t* out, int64_t capacity, void* stream,
+                  int64_t* n_written, int64_t* next_task);
 
 /* gp_count without any memory allocation, for callers that cannot allocate
  * device memory when they count (an arena or pool owns the device memory,

@@ -54,6 +54,8 @@ def _load():
         lib.oracle_count.argtypes = [i32, P, i32, P, P, i32, P]
         lib.oracle_count_restricted.argtypes = [i32, P, P, i32, P, i32, P, P, i32, i32, i32, P, P]
         lib.oracle_triangles.argtypes = [i32, P, P, i32, P]
+        lib.oracle_list_restricted.argtypes = [i32, P, P, i32, P, i32, P, P, i32, i32, P, i64, P]
+        lib.oracle_list_restricted.restype = ctypes.c_int
         for f in (lib.oracle_build_csr, lib.oracle_aut_count, lib.oracle_count_maps,
                   lib.oracle_count, lib.oracle_count_restricted, lib.oracle_triangles):
             f.restype = ctypes.c_int
@@ -156,6 +158,27 @@ def count_restricted(adj, order, restrictions, g, threads=None, root_begin=0, ro
     if rc:
         raise ValueError(f"oracle_count_restricted failed ({rc})")
     return (int(hi[0]) << 64) | int(lo[0])
+
+
+def list_restricted(adj, order, restrictions, g, root_begin=0, root_end=None, cap=1 << 22):
+    """Embeddings (k-tuples, entry a = image of pattern vertex a) found in
+    matching order `order` under the restrictions; returns (array, total)."""
+    adj = _adj(adj)
+    k = adj.shape[0]
+    order = np.ascontiguousarray(order, dtype=np.int32)
+    res = np.ascontiguousarray(np.array(restrictions, dtype=np.int32).reshape(-1, 2))
+    nres = res.shape[0]
+    if nres == 0:
+        res = np.zeros((1, 2), dtype=np.int32)
+    out = np.zeros((max(1, cap), k), dtype=np.int32)
+    n_out = np.zeros(1, dtype=np.int64)
+    rc = _load().oracle_list_restricted(k, _p(adj), _p(order), nres, _p(res), g.n, _p(g.row_ptr),
+                                        _p(g.col), root_begin, g.n if root_end is None else root_end,
+                                        _p(out), cap, _p(n_out))
+    if rc:
+        raise ValueError(f"oracle_list_restricted failed ({rc})")
+    total = int(n_out[0])
+    return out[: min(total, cap)].copy(), total
 
 
 def degree_relabel(g):

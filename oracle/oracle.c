@@ -288,6 +288,57 @@ int oracle_count_restricted(int32_t k, const uint8_t* adj, const int32_t* order,
     return 0;
 }
 
+/* ------------------------------------------------------------------ listing */
+
+typedef struct { int32_t* out; int64_t cap; int64_t n; } list_sink;
+
+static void list_walk(const walk_t* w, int d, int32_t* img, list_sink* sink) {
+    if (d == w->k) {                             /* one embedding */
+        if (sink->n < sink->cap)
+            for (int j = 0; j < w->k; ++j) sink->out[sink->n * w->k + w->order[j]] = img[j];
+        sink->n++;
+        return;
+    }
+    int32_t a = img[w->anchor[d]];
+    for (int64_t e = w->row_ptr[a]; e < w->row_ptr[a + 1]; ++e) {
+        int32_t v = w->col[e];
+        int ok = 1;
+        for (int j = 0; j < d && ok; ++j) if (img[j] == v) ok = 0;
+        for (int c = 0; c < w->nchk[d] && ok; ++c)
+            if (!has_edge(w, img[w->chk[d][c]], v)) ok = 0;
+        for (int r = 0; r < w->nres[d] && ok; ++r) {
+            int32_t o = img[w->res_other[d][r]];
+            if (w->res_gt[d][r] ? !(v > o) : !(v < o)) ok = 0;
+        }
+        if (!ok) continue;
+        img[d] = v;
+        list_walk(w, d + 1, img, sink);
+    }
+}
+
+int oracle_list_restricted(int32_t k, const uint8_t* adj, const int32_t* order,
+                           int32_t nres, const int32_t* res,
+                           int32_t n, const int64_t* row_ptr, const int32_t* col,
+                           int32_t root_begin, int32_t root_end,
+                           int32_t* out, int64_t cap, int64_t* n_out) {
+    if (!order || (nres > 0 && !res) || nres < 0 || !n_out || cap < 0 || (cap > 0 && !out)) return -1;
+    walk_t* w = (walk_t*)malloc(sizeof(walk_t));
+    if (!w) return -2;
+    int rc = setup_walk(w, k, adj, order, nres, res, n, row_ptr, col);
+    if (rc) { free(w); return rc; }
+    if (root_begin < 0) root_begin = 0;
+    if (root_end > n) root_end = n;
+    list_sink sink = {out, cap, 0};
+    int32_t img[8];
+    for (int32_t r = root_begin; r < root_end; ++r) {
+        img[0] = r;
+        list_walk(w, 1, img, &sink);
+    }
+    *n_out = sink.n;
+    free(w);
+    return 0;
+}
+
 /* ---------------------------------------------------------------- triangles */
 
 typedef struct {

@@ -67,6 +67,17 @@ int oracle_count_restricted(int32_t k, const uint8_t* adj, const int32_t* order,
                             int32_t root_begin, int32_t root_end,
                             int32_t nthreads, uint64_t* hi, uint64_t* lo);
 
+/* The embeddings found by oracle_count_restricted with roots in
+ * [root_begin, root_end), single-threaded in depth-first order: embedding i
+ * is written as out[i * k + a] = image of pattern vertex a, for at most cap
+ * embeddings. *n_out receives how many there are in total (also beyond
+ * cap). Listing is the enumeration of Section II-A, one tuple per embedding. */
+int oracle_list_restricted(int32_t k, const uint8_t* adj, const int32_t* order,
+                           int32_t nres, const int32_t* res,
+                           int32_t n, const int64_t* row_ptr, const int32_t* col,
+                           int32_t root_begin, int32_t root_end,
+                           int32_t* out, int64_t cap, int64_t* n_out);
+
 /* Unordered triangles {a, b, c} of the graph (the cost model's tri_cnt,
  * Section IV-C, counts each triangle once per ordered traversal; see the
  * planner). */

@@ -58,6 +58,7 @@ SIGNATURES = {
     "gp_count_batch_ranges": (i32, [P, P, P, P, P, i32, P, P, P, P]),
     "gp_count_scratch_bytes": (i32, [P, P, i32, P, P]),
     "gp_count_noalloc": (i32, [P, P, i32, P, P]),
+    "gp_list": (i32, [P, P, i32, i64, i64, P, i64, P, P, P]),
     "gp_status_str": (ctypes.c_char_p, [i32]),
     "gp_last_error": (ctypes.c_char_p, []),
     "gp_take_launch_count": (i64, []),
@@ -256,6 +257,15 @@ def gp_count_noalloc(graph, schedules, idx=0, stream=None):
     check(lib().gp_count_noalloc(graph.h, schedules.h, idx, _stream(stream), ctypes.byref(out)),
           "gp_count_noalloc")
     return out.value
+
+
+def gp_list(graph, schedules, idx, task_begin, task_end, out, capacity, stream=None):
+    """List embeddings into the device buffer `out` (capacity x k int32, e.g.
+    a torch tensor). Returns (status, n_written, next_task)."""
+    nw, nt = ctypes.c_int64(), ctypes.c_int64()
+    st = check(lib().gp_list(graph.h, schedules.h, idx, int(task_begin), int(task_end), _ptr(out), int(capacity),
+                             _stream(stream), ctypes.byref(nw), ctypes.byref(nt)), "gp_list")
+    return st, nw.value, nt.value
 
 
 def gp_take_launch_count():

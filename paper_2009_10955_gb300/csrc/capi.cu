@@ -655,6 +655,30 @@ gp_status gp_schedule_set_iep(gp_schedules* s, int32_t enable, int32_t* n_iep) {
     return GP_OK;
 }
 
+gp_status gp_list(gp_graph* g, const gp_schedules* s, int32_t idx, int64_t task_begin,
+                  int64_t task_end, int32_t* out, int64_t capacity, void* stream,
+                  int64_t* n_written, int64_t* next_task) {
+    if (!n_written || !next_task || capacity < 0 || (capacity > 0 && !out)) return fail(GP_ERR_ARG, "bad argument");
+    gp_count_opts r;
+    std::memset(&r, 0, sizeof(r));
+    r.struct_size = sizeof(r);
+    r.task_begin = task_begin;
+    r.task_end = task_end;
+    CountJob job;
+    gp_status rc = make_job(g, s, idx, &r, &job);
+    if (rc != GP_OK) return rc;
+    if (job.plan.iep) return fail(GP_ERR_ARG, "inclusion-exclusion plans count; they cannot list");
+    rc = ensure_device(g);
+    if (rc != GP_OK) return rc;
+    int64_t written = 0, cut = 0;
+    rc = run_list(job, out, capacity, static_cast<cudaStream_t>(stream), &written, &cut);
+    if (rc != GP_OK) return rc;
+    if (cut == 0 && job.ntasks > 0) return fail(GP_ERR_SCRATCH, "the first task's embeddings exceed the capacity");
+    *n_written = written;
+    *next_task = job.task_begin + cut;
+    return cut == job.ntasks ? GP_OK : GP_PARTIAL;
+}
+
 gp_status gp_count_scratch_bytes(const gp_graph* g, const gp_schedules* s, int32_t idx,
                                  const gp_count_opts* opts, uint64_t* bytes) {
     if (!g || !s || !bytes) return fail(GP_ERR_ARG, "null argument");

@@ -30,6 +30,8 @@
 #include <climits>
 #include <vector>
 
+#include <cub/device/device_scan.cuh>
+
 #include "engine.h"
 
 namespace gp {
@@ -765,7 +767,8 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
     c.lane = lane;
     c.lane_work = lane_work;
     c.deadline = &s_deadline[w];
-    c.lane_bitmap = lane_bitmap != 0;
+    c.lane_bitmap = lane_bitmap == 1;
+    const int bitmap_mode = lane_bitmap;    // 0 warp, 1 lane, 2 by pattern size
     c.task_cycles = task_cycles;
     c.job_abort = aborts;
     if (lane == 0) s_deadline[w] = 0;
@@ -831,6 +834,9 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
                 c.col = J.col;
                 c.core_bits = J.core_bits;
                 c.core_n = (use_core && J.core_bits) ? J.core_n : 0;
+                // one candidate per lane pays off when the last level runs
+                // below two bitmap loops (k >= 5); 4-vertex plans prefer a warp
+                c.lane_bitmap = bitmap_mode == 1 || (bitmap_mode == 2 && J.plan.k >= 5);
                 if (c.core_n == 0 || J.core_words > c.bm_stride) c.bm = nullptr;
                 else if (bm_stride > 0 && !kStats && J.plan.k - 1 <= bm_sets)
                     c.bm = s_bitmaps + (size_t)w * bm_sets * bm_stride;
@@ -922,6 +928,161 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
         for (int o = 16; o; o >>= 1) my_bytes += __shfl_down_sync(kFull, my_bytes, o);
         if (lane == 0 && my_bytes) atomicAdd(stats, my_bytes);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Listing (every embedding as a k-tuple). One warp per edge task, the loops
+// of run_task without the per-lane and bitmap shortcuts; the last level's
+// candidate set is materialised (in the spare slot `nslots`) and every
+// element that is not an already-matched vertex is one embedding. Pass 1
+// (kWrite = false) stores each task's embedding count; pass 2 writes task
+// t's tuples from offset[t], in depth-first order, so the output is
+// deterministic.
+
+__device__ __forceinline__ int list_last(const TaskCtx& c, const int* v, int32_t* out, int64_t at,
+                                         bool write) {
+    const GpPlan& P = *c.P;
+    const int L = P.k - 1;
+    const GpLevel& lv = P.lvl[L];
+    const Window w = window(lv.lo_mask, lv.hi_mask, v);
+    List S;
+    if (P.last_count_only) {
+        const List a = (P.last_base_kind == 1) ? nbr(c, v[P.last_base]) : slot(c, P.last_base);
+        int32_t* spare = c.slots + (size_t)P.nslots * c.slot_cap;
+        const int m = warp_intersect(c, a, nbr(c, v[L - 1]), w, spare, c.slot_cap, nullptr);
+        __syncwarp();
+        S = List{spare, m, -1};
+    } else {
+        S = clip((lv.src_kind == 1) ? nbr(c, v[lv.src]) : slot(c, lv.src), w);
+    }
+    int total = 0;
+    for (int base = 0; base < S.n; base += 32) {
+        const int i = base + c.lane;
+        int x = -1;
+        bool keep = false;
+        if (i < S.n) {
+            x = __ldg(S.p + i);
+            keep = true;
+            for (int j = 0; j < L; ++j) keep &= !((lv.excl_mask >> j & 1) && v[j] == x);
+        }
+        const unsigned m = __ballot_sync(kFull, keep);
+        if (write && keep) {
+            int32_t* t = out + (at + total + __popc(m & lanemask_lt())) * P.k;
+            for (int d = 0; d < L; ++d) t[P.order[d]] = v[d];
+            t[P.order[L]] = x;
+        }
+        total += __popc(m);
+    }
+    return total;
+}
+
+template <bool kWrite>
+__global__ void __launch_bounds__(kWarps * 32, 4)
+k_list(const CountJob* __restrict__ job, int64_t ntasks, unsigned long long* __restrict__ cursor,
+       int64_t* __restrict__ per_task, int32_t* __restrict__ out, int32_t* __restrict__ slot_pool,
+       int64_t warp_elems, int* __restrict__ err) {
+    __shared__ GpPlan s_plan[kWarps];
+    __shared__ int s_len[kWarps][GP_MAX_SLOTS];
+    __shared__ long long s_deadline[kWarps];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * kWarps + w;
+    {
+        const int* src = reinterpret_cast<const int*>(&job->plan);
+        int* dst = reinterpret_cast<int*>(&s_plan[w]);
+        for (int i = lane; i < (int)(sizeof(GpPlan) / 4); i += 32) dst[i] = src[i];
+        if (lane == 0) s_deadline[w] = 0;
+        __syncwarp();
+    }
+    TaskCtx c;
+    c.P = &s_plan[w];
+    c.row_ptr = job->row_ptr;
+    c.col = job->col;
+    c.core_bits = job->core_bits;
+    c.core_n = job->core_bits ? job->core_n : 0;
+    c.core_words = job->core_words;
+    c.slots = slot_pool + gw * warp_elems;
+    c.slot_cap = job->slot_cap;
+    c.n_vertices = job->n;
+    c.slen = s_len[w];
+    c.bm = nullptr;
+    c.bm_stride = 0;
+    c.lane_bitmap = false;
+    c.lane = lane;
+    c.lane_work = kLaneWork;
+    c.err = err;
+    c.sbytes = nullptr;
+    c.deadline = &s_deadline[w];
+    c.task_cycles = 0;
+    c.job_abort = err;
+    const GpPlan& P = s_plan[w];
+    const int k = P.k;
+    for (;;) {
+        unsigned long long t0 = 0;
+        if (lane == 0) t0 = atomicAdd(cursor, 1ull);
+        t0 = __shfl_sync(kFull, t0, 0);
+        if ((int64_t)t0 >= ntasks) break;
+        const int64_t e = job->task_begin + (int64_t)t0;
+        int rl = 0, rh = c.n_vertices - 1;           // source vertex of entry e
+        while (rl < rh) {
+            int mid = (rl + rh + 1) >> 1;
+            if (__ldg(c.row_ptr + mid) <= e) rl = mid; else rh = mid - 1;
+        }
+        int v[GP_MAX_K];
+#pragma unroll
+        for (int i = 0; i < GP_MAX_K; ++i) v[i] = -1;
+        v[0] = rl;
+        v[1] = __ldg(c.col + e);
+        int64_t found = 0;
+        const int64_t at = kWrite ? per_task[t0] : 0;
+        const bool ok1 = !((P.lvl[1].lo_mask & 1) && !(v[1] > v[0])) && !((P.lvl[1].hi_mask & 1) && !(v[1] < v[0]));
+        if (ok1) {
+            run_builds(c, 1, v);
+            if (k == 3) {
+                found += list_last(c, v, out, at + found, kWrite);
+            } else {
+                List lst[GP_MAX_K];
+                int cur[GP_MAX_K];
+                int d = 2;
+                lst[2] = clip((P.lvl[2].src_kind == 1) ? nbr(c, v[P.lvl[2].src]) : slot(c, P.lvl[2].src),
+                              window(P.lvl[2].lo_mask, P.lvl[2].hi_mask, v));
+                cur[2] = 0;
+                while (d >= 2) {
+                    if (cur[d] >= lst[d].n) { --d; continue; }
+                    const int x = __ldg(lst[d].p + cur[d]);
+                    ++cur[d];
+                    const uint8_t ex = P.lvl[d].excl_mask;
+                    bool skip = false;
+                    for (int j = 0; j < d; ++j) skip |= ((ex >> j) & 1) && v[j] == x;
+                    if (skip) continue;
+                    v[d] = x;
+                    run_builds(c, d, v);
+                    if (d == k - 2) {
+                        found += list_last(c, v, out, at + found, kWrite);
+                    } else {
+                        ++d;
+                        const GpLevel& L2 = P.lvl[d];
+                        lst[d] = clip((L2.src_kind == 1) ? nbr(c, v[L2.src]) : slot(c, L2.src),
+                                      window(L2.lo_mask, L2.hi_mask, v));
+                        cur[d] = 0;
+                    }
+                }
+            }
+        }
+        if (!kWrite && lane == 0) per_task[t0] = found;
+    }
+}
+
+// Largest c <= ntasks with offsets[c] <= capacity (offsets is an exclusive
+// prefix sum with ntasks + 1 entries): out[0] = c, out[1] = offsets[c].
+__global__ void k_list_cut(const int64_t* __restrict__ offsets, int64_t ntasks, int64_t capacity,
+                           int64_t* __restrict__ out) {
+    int64_t lo = 0, hi = ntasks;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (offsets[mid] <= capacity) lo = mid; else hi = mid - 1;
+    }
+    out[0] = lo;
+    out[1] = offsets[lo];
 }
 
 }  // namespace
@@ -1052,7 +1213,7 @@ gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& opt, cuda
                                                       warp_elems, chunk, (long long)opt.budget_cycles,
                                                       d_err, d_stats, opt.lane_work > 0 ? opt.lane_work : kLaneWork,
                                                       opt.no_core ? 0 : 1, geo.bm_stride, geo.bm_sets,
-                                                      (long long)opt.task_cycles, d_aborts, opt.warp_bitmap ? 0 : 1);
+                                                      (long long)opt.task_cycles, d_aborts, opt.warp_bitmap ? 0 : 2);
         count_launch();
         e = cudaGetLastError();
     }
@@ -1135,7 +1296,7 @@ gp_status run_count_in_scratch(const CountJob* jobs, int njobs, void* d_scratch,
     if (total > 0) {
         kern<<<(unsigned)blocks, kWarps * 32, 0, st>>>(d_jobs, njobs, total, d_cursor, d_res, d_slots,
                                                       warp_elems, chunk, 0, d_err, d_stats, kLaneWork, 1, 0, 0,
-                                                      0, d_aborts, 1);
+                                                      0, d_aborts, 2);
         count_launch();
         GP_CUDA_TRY(cudaGetLastError());
     }
@@ -1147,6 +1308,83 @@ gp_status run_count_in_scratch(const CountJob* jobs, int njobs, void* d_scratch,
         return GP_ERR_INTERNAL;
     }
     for (int j = 0; j < 2 * njobs; ++j) results[j] = h_res[j];
+    return GP_OK;
+}
+
+gp_status run_list(const CountJob& job, int32_t* d_out, int64_t capacity, cudaStream_t st,
+                   int64_t* n_written, int64_t* cut_tasks) {
+    const int64_t T = job.ntasks;
+    *n_written = 0;
+    *cut_tasks = 0;
+    if (T == 0) return GP_OK;
+    int dev = 0, nsm = 0, occ = 0;
+    GP_CUDA_TRY(cudaGetDevice(&dev));
+    GP_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    GP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_list<false>, kWarps * 32, 0));
+    const int64_t warp_elems = (int64_t)(job.plan.nslots + 1) * job.slot_cap;
+    const size_t per_block = (size_t)kWarps * (size_t)warp_elems * sizeof(int32_t);
+    size_t free_b = 0, total_b = 0;
+    GP_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    int64_t blocks = (int64_t)nsm * std::max(occ, 1);
+    while (blocks > nsm && per_block * (size_t)blocks > free_b / 4) blocks -= nsm;
+    if (per_block * (size_t)blocks > free_b / 2) { set_error("listing scratch does not fit"); return GP_ERR_SCRATCH; }
+    size_t scan_b = 0;
+    GP_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, scan_b, (int64_t*)nullptr, (int64_t*)nullptr, T + 1, st));
+    void* mem = nullptr;
+    const size_t head_b = 256;                       // job, cursor, error, cut
+    const size_t cnt_b = sizeof(int64_t) * (size_t)(T + 1);
+    GP_CUDA_TRY(cudaMallocAsync(&mem, head_b + sizeof(CountJob) + 2 * cnt_b + scan_b + 64, st));
+    int32_t* slots = nullptr;
+    if (cudaMallocAsync((void**)&slots, per_block * (size_t)blocks, st) != cudaSuccess) {
+        cudaFreeAsync(mem, st);
+        cudaGetLastError();
+        set_error("cannot allocate listing scratch");
+        return GP_ERR_NOMEM;
+    }
+    char* b = static_cast<char*>(mem);
+    unsigned long long* cursor = reinterpret_cast<unsigned long long*>(b);
+    int* err = reinterpret_cast<int*>(b + 8);
+    int64_t* cut = reinterpret_cast<int64_t*>(b + 16);
+    CountJob* d_job = reinterpret_cast<CountJob*>(b + head_b);
+    int64_t* counts = reinterpret_cast<int64_t*>(b + head_b + ((sizeof(CountJob) + 63) & ~(size_t)63));
+    int64_t* offsets = counts + (T + 1);
+    void* scan_tmp = offsets + (T + 1);
+    int64_t h[2] = {0, 0};
+    int h_err = 0;
+    cudaError_t e = cudaMemsetAsync(b, 0, head_b, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_job, &job, sizeof(CountJob), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, cnt_b, st);
+    if (e == cudaSuccess) {
+        k_list<false><<<(unsigned)blocks, kWarps * 32, 0, st>>>(d_job, T, cursor, counts, nullptr, slots,
+                                                               warp_elems, err);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cub::DeviceScan::ExclusiveSum(scan_tmp, scan_b, counts, offsets, T + 1, st);
+    if (e == cudaSuccess) {
+        k_list_cut<<<1, 1, 0, st>>>(offsets, T, capacity, cut);
+        count_launch(2);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, cut, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && h[0] > 0) {
+        e = cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), st);
+        if (e == cudaSuccess) {
+            k_list<true><<<(unsigned)blocks, kWarps * 32, 0, st>>>(d_job, h[0], cursor, offsets, d_out, slots,
+                                                                  warp_elems, err);
+            count_launch();
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(slots, st);
+    cudaFreeAsync(mem, st);
+    if (e != cudaSuccess) { set_error("listing kernels failed: %s", cudaGetErrorString(e)); return GP_ERR_CUDA; }
+    if (h_err) { set_error("listing kernel reported internal error %d", h_err); return GP_ERR_INTERNAL; }
+    *cut_tasks = h[0];
+    *n_written = h[1];
     return GP_OK;
 }
 

@@ -110,6 +110,12 @@ gp_status single_job(gp_graph* g, const gp_schedules* s, int32_t idx, CountJob* 
 // divided by their multiplicity); GP_ERR_OVERFLOW beyond 64 bits (capi.cu).
 gp_status job_total(const CountJob& job, const uint64_t* res, uint64_t* out);
 
+// Listing: the embeddings of the longest prefix of the job's tasks whose
+// total fits `capacity` tuples, written to d_out (k int32 per embedding).
+// *cut_tasks receives that prefix's length, *n_written its embeddings.
+gp_status run_list(const CountJob& job, int32_t* d_out, int64_t capacity, cudaStream_t st,
+                   int64_t* n_written, int64_t* cut_tasks);
+
 // Device scratch run_count would allocate for these jobs and options.
 gp_status scratch_bytes(const CountJob* jobs, int njobs, const LaunchOpts& lo, uint64_t* bytes);
 

@@ -52,7 +52,7 @@ class Server:
     """Continuous batching over device-resident graphs (see module doc)."""
 
     def __init__(self, graphs, slice_ms=20.0, max_batch=256, mem_budget=None, stream=None,
-                 clock_ghz=1.9, max_slices=None, item_ms=None):
+                 clock_ghz=1.9, max_slices=None, item_ms=None, deadline_s=None):
         self.graphs = dict(graphs)
         self.slice_cycles = int(slice_ms * 1e-3 * clock_ghz * 1e9)
         # with item_ms, a single work item (edge task) that needs longer than
@@ -63,6 +63,7 @@ class Server:
         self.mem_budget = mem_budget
         self.stream = stream
         self.max_slices = max_slices
+        self.deadline_s = deadline_s      # wall-clock limit per request (from arrival)
         self._plans = {}
         self._pending = collections.deque()
         self._active = []
@@ -163,6 +164,10 @@ class Server:
                         r.done.set()
                     elif self.max_slices is not None and r.slices >= self.max_slices:
                         r.error = TimeoutError(f"request {r.rid} exceeded {self.max_slices} slices")
+                        r.finish = now
+                        r.done.set()
+                    elif self.deadline_s is not None and now - r.arrival > self.deadline_s:
+                        r.error = TimeoutError(f"request {r.rid} exceeded its {self.deadline_s} s deadline")
                         r.finish = now
                         r.done.set()
                     else:

@@ -341,3 +341,27 @@ def test_cardinality_estimates_match_graph_means():
     assert abs(n * p1 - A.sum(axis=1).mean()) < 1e-9
     common = (A @ A)[A == 1]
     assert abs(n * p1 * p2 - common.mean()) < 1e-9
+
+
+def test_listing_is_the_set_of_embeddings():
+    # every listed tuple is an edge-preserving injective map obeying the
+    # restrictions, they are pairwise distinct, and there are count(P, G)
+    # of them; brute force gives the same set
+    n = 9
+    s, d = er_edges(n, 22, seed=3)
+    g = oracle.build_csr(n, s, d)
+    gadj = dense(g)
+    for name in ("house", "c4", "diamond", "path4"):
+        p = named_pattern(name)
+        adj = p.tolist()
+        k = len(adj)
+        sched = pr.efficient_schedules(adj)[0][0]
+        rs = pr.restriction_sets(adj)[0]
+        tuples, total = oracle.list_restricted(p, sched, rs, g)
+        assert total == len(tuples) == oracle.count(p, g)
+        got = {tuple(t) for t in tuples}
+        assert len(got) == total
+        pe = [(a, b) for a in range(k) for b in range(k) if adj[a][b]]
+        brute = {t for t in itertools.permutations(range(n), k)
+                 if all(gadj[t[a], t[b]] for a, b in pe) and all(t[a] > t[b] for a, b in rs)}
+        assert got == brute
