@@ -118,6 +118,21 @@ void gp_graph_destroy(gp_graph* g);
  * Computes the automorphism group (Section IV-A) on creation. */
 gp_status gp_pattern_create(const uint8_t* adj, int32_t k, gp_pattern** out);
 
+/* Vertex-labelled pattern (Section II-A: the method extends to labelled
+ * graphs): as gp_pattern_create, plus labels[k]; a vertex matched to
+ * pattern vertex a must carry labels[a], and automorphisms must preserve
+ * labels. Labelled plans are counted by gp_count (which runs them through
+ * the listing kernel's counting pass, without the bit-matrix shortcuts) and
+ * listed by gp_list; the batched, time-sliced and no-allocation calls
+ * reject them. */
+gp_status gp_pattern_create_labeled(const uint8_t* adj, const int32_t* labels, int32_t k,
+                                    gp_pattern** out);
+
+/* Attach vertex labels to a graph: labels (host) has n entries in the
+ * labelling of the input pairs (the library applies its degree relabel).
+ * Replaces earlier labels. Synchronous. */
+gp_status gp_graph_set_labels(gp_graph* g, const int32_t* labels, void* stream);
+
 /* |Aut(P)|: permutations of V_p that preserve E_p. */
 gp_status gp_pattern_aut_count(const gp_pattern* p, uint64_t* out);
 

@@ -56,6 +56,10 @@ def _load():
         lib.oracle_triangles.argtypes = [i32, P, P, i32, P]
         lib.oracle_list_restricted.argtypes = [i32, P, P, i32, P, i32, P, P, i32, i32, P, i64, P]
         lib.oracle_list_restricted.restype = ctypes.c_int
+        lib.oracle_aut_count_labeled.argtypes = [i32, P, P, P]
+        lib.oracle_aut_count_labeled.restype = ctypes.c_int
+        lib.oracle_count_labeled.argtypes = [i32, P, P, i32, P, P, P, i32, P]
+        lib.oracle_count_labeled.restype = ctypes.c_int
         for f in (lib.oracle_build_csr, lib.oracle_aut_count, lib.oracle_count_maps,
                   lib.oracle_count, lib.oracle_count_restricted, lib.oracle_triangles):
             f.restype = ctypes.c_int
@@ -179,6 +183,29 @@ def list_restricted(adj, order, restrictions, g, root_begin=0, root_end=None, ca
         raise ValueError(f"oracle_list_restricted failed ({rc})")
     total = int(n_out[0])
     return out[: min(total, cap)].copy(), total
+
+
+def aut_count_labeled(adj, plabels):
+    adj = _adj(adj)
+    pl = np.ascontiguousarray(plabels, dtype=np.int32)
+    out = np.zeros(1, dtype=np.uint64)
+    rc = _load().oracle_aut_count_labeled(adj.shape[0], _p(adj), _p(pl), _p(out))
+    if rc:
+        raise ValueError(f"oracle_aut_count_labeled failed ({rc})")
+    return int(out[0])
+
+
+def count_labeled(adj, plabels, g, glabels, threads=None):
+    """Embeddings of a vertex-labelled pattern in a vertex-labelled graph."""
+    adj = _adj(adj)
+    pl = np.ascontiguousarray(plabels, dtype=np.int32)
+    gl = np.ascontiguousarray(glabels, dtype=np.int32)
+    out = np.zeros(1, dtype=np.uint64)
+    rc = _load().oracle_count_labeled(adj.shape[0], _p(adj), _p(pl), g.n, _p(g.row_ptr), _p(g.col), _p(gl),
+                                      threads or default_threads(), _p(out))
+    if rc:
+        raise ValueError(f"oracle_count_labeled failed ({rc})")
+    return int(out[0])
 
 
 def degree_relabel(g):

@@ -92,6 +92,8 @@ typedef struct {
     const int64_t* row_ptr;
     const int32_t* col;
     int32_t root_begin, root_end, root_stride;
+    const int32_t* glab;   /* graph vertex labels, or NULL (unlabelled)        */
+    int32_t plab[8];       /* label required at depth d                        */
     atomic_long cursor;    /* next root index (in stride units) to hand out */
 } walk_t;
 
@@ -118,6 +120,7 @@ static u128 walk(const walk_t* w, int d, int32_t* img) {
             int32_t o = img[w->res_other[d][r]];
             if (w->res_gt[d][r] ? !(v > o) : !(v < o)) ok = 0;               /* restriction */
         }
+        if (ok && w->glab && w->glab[v] != w->plab[d]) ok = 0;             /* label */
         if (!ok) continue;
         img[d] = v;
         total += walk(w, d + 1, img);
@@ -139,6 +142,7 @@ static void* worker_main(void* arg) {
         long e = s + chunk < count ? s + chunk : count;
         for (long i = s; i < e; ++i) {
             img[0] = (int32_t)(w->root_begin + i * w->root_stride);
+            if (w->glab && w->glab[img[0]] != w->plab[0]) continue;             /* root label */
             me->sum += walk(w, 1, img);
         }
     }
@@ -285,6 +289,53 @@ int oracle_count_restricted(int32_t k, const uint8_t* adj, const int32_t* order,
     free(w);
     if (rc) return rc;
     split128(total, hi, lo);
+    return 0;
+}
+
+/* --------------------------------------------------------------- labelled */
+
+int oracle_aut_count_labeled(int32_t k, const uint8_t* adj, const int32_t* plabels, uint64_t* out) {
+    if (k < 1 || k > 10 || !adj || !plabels || !out) return -1;
+    int p[10];
+    for (int i = 0; i < k; ++i) p[i] = i;
+    uint64_t c = 0;
+    do {
+        int ok = 1;
+        for (int a = 0; a < k && ok; ++a) {
+            if (plabels[p[a]] != plabels[a]) ok = 0;
+            for (int b = 0; b < k && ok; ++b)
+                if (adj[a * k + b] && !adj[p[a] * k + p[b]]) ok = 0;
+        }
+        c += (uint64_t)ok;
+    } while (next_perm(p, k));
+    *out = c;
+    return 0;
+}
+
+int oracle_count_labeled(int32_t k, const uint8_t* adj, const int32_t* plabels,
+                         int32_t n, const int64_t* row_ptr, const int32_t* col,
+                         const int32_t* glabels, int32_t nthreads, uint64_t* out) {
+    if (!plabels || !glabels || !out) return -1;
+    uint64_t aut;
+    int rc = oracle_aut_count_labeled(k, adj, plabels, &aut);
+    if (rc) return rc;
+    int32_t order[8];
+    if (bfs_order(k, adj, order)) return -1;
+    walk_t* w = (walk_t*)malloc(sizeof(walk_t));
+    if (!w) return -2;
+    rc = setup_walk(w, k, adj, order, 0, NULL, n, row_ptr, col);
+    if (rc) { free(w); return rc; }
+    w->glab = glabels;
+    for (int d = 0; d < k; ++d) w->plab[d] = plabels[order[d]];
+    w->root_begin = 0; w->root_end = n; w->root_stride = 1;
+    u128 maps = 0;
+    rc = run_walk(w, nthreads, &maps);
+    free(w);
+    if (rc) return rc;
+    if (maps % aut) return -3;
+    u128 q = maps / aut;
+    if (q >> 64) return -4;
+    *out = (uint64_t)q;
     return 0;
 }
 

@@ -78,6 +78,17 @@ int oracle_list_restricted(int32_t k, const uint8_t* adj, const int32_t* order,
                            int32_t root_begin, int32_t root_end,
                            int32_t* out, int64_t cap, int64_t* n_out);
 
+/* Vertex-labelled patterns and graphs (Section II-A notes that the method
+ * extends to labelled graphs): a map must also send every pattern vertex to
+ * a graph vertex of the same label. plabels has k entries, glabels n.
+ * oracle_aut_count_labeled counts the automorphisms that preserve labels;
+ * oracle_count_labeled returns maps / labelled |Aut| (-3 / -4 as for
+ * oracle_count). */
+int oracle_aut_count_labeled(int32_t k, const uint8_t* adj, const int32_t* plabels, uint64_t* out);
+int oracle_count_labeled(int32_t k, const uint8_t* adj, const int32_t* plabels,
+                         int32_t n, const int64_t* row_ptr, const int32_t* col,
+                         const int32_t* glabels, int32_t nthreads, uint64_t* out);
+
 /* Unordered triangles {a, b, c} of the graph (the cost model's tri_cnt,
  * Section IV-C, counts each triangle once per ordered traversal; see the
  * planner). */

@@ -47,11 +47,13 @@ def _edges(adj):
     return [(a, b) for a in range(k) for b in range(k) if adj[a][b]]
 
 
-def automorphisms(adj):
-    """All permutations preserving the edge set (Section IV-A)."""
+def automorphisms(adj, labels=None):
+    """All permutations preserving the edge set (Section IV-A), and the
+    vertex labels when the pattern is labelled."""
     k = len(adj)
     E = _edges(adj)
-    return [p for p in permutations(range(k)) if all(adj[p[a]][p[b]] for a, b in E)]
+    return [p for p in permutations(range(k)) if all(adj[p[a]][p[b]] for a, b in E)
+            and (labels is None or all(labels[p[a]] == labels[a] for a in range(k)))]
 
 
 def _acyclic(k, arcs):
@@ -97,11 +99,11 @@ def validate(k, aut_count, res_set):
     return linear_extensions(k, res_set) * aut_count == factorial(k)
 
 
-def restriction_sets(adj):
+def restriction_sets(adj, labels=None):
     """Algorithm 1 (res_set_generation): every restriction set it returns,
     as a sorted list of sorted tuples of pairs."""
     k = len(adj)
-    auts = automorphisms(adj)
+    auts = automorphisms(adj, labels)
     n_aut = len(auts)
 
     @lru_cache(maxsize=None)

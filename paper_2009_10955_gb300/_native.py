@@ -43,6 +43,8 @@ SIGNATURES = {
     "gp_graph_destroy": (None, [P]),
     "gp_pattern_create": (i32, [P, i32, P]),
     "gp_pattern_aut_count": (i32, [P, P]),
+    "gp_pattern_create_labeled": (i32, [P, P, i32, P]),
+    "gp_graph_set_labels": (i32, [P, P, P]),
     "gp_pattern_restriction_sets": (i32, [P, i32, P, i32, P, P]),
     "gp_pattern_schedules": (i32, [P, P, P, i32, P]),
     "gp_pattern_destroy": (None, [P]),
@@ -181,6 +183,20 @@ def gp_pattern_create(adj):
     h = ctypes.c_void_p()
     check(lib().gp_pattern_create(_ptr(adj), adj.shape[0], ctypes.byref(h)), "gp_pattern_create")
     return Pattern(h, adj.shape[0])
+
+
+def gp_pattern_create_labeled(adj, labels):
+    adj = np.ascontiguousarray(adj, dtype=np.uint8)
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    h = ctypes.c_void_p()
+    check(lib().gp_pattern_create_labeled(_ptr(adj), _ptr(lab), adj.shape[0], ctypes.byref(h)),
+          "gp_pattern_create_labeled")
+    return Pattern(h, adj.shape[0])
+
+
+def gp_graph_set_labels(graph, labels, stream=None):
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    check(lib().gp_graph_set_labels(graph.h, _ptr(lab), _stream(stream)), "gp_graph_set_labels")
 
 
 def gp_schedule(pattern, graph=None, top_k=1, stream=None):

@@ -55,6 +55,7 @@ struct DevBuf {
 
 void free_graph(gp_graph* g) {
     if (!g) return;
+    if (g->labels) cudaFree(g->labels);
     if (g->row_ptr) cudaFree(g->row_ptr);
     if (g->col) cudaFree(g->col);
     if (g->perm) cudaFree(g->perm);
@@ -133,6 +134,8 @@ gp_status make_job(gp_graph* g, const gp_schedules* s, int32_t idx, const gp_cou
     job->core_bits = g->core_bits;
     job->core_n = g->core_n;
     job->core_words = g->core_words;
+    job->labels = g->labels;
+    if (job->plan.labeled && !g->labels) return fail(GP_ERR_ARG, "labelled pattern on a graph without labels");
     return GP_OK;
 }
 
@@ -157,7 +160,8 @@ std::unique_ptr<PatternInfo> clone_pattern(const PatternInfo& p) {
     for (int a = 0; a < p.k; ++a)
         for (int b = 0; b < p.k; ++b) adj[a * p.k + b] = p.adj[a][b];
     std::string err;
-    if (!pattern_init(*q, adj, p.k, err)) q.reset();
+    const bool ok = p.labeled ? pattern_init_labeled(*q, adj, p.labels, p.k, err) : pattern_init(*q, adj, p.k, err);
+    if (!ok) q.reset();
     return q;
 }
 
@@ -185,6 +189,7 @@ bool opts_ok(const gp_count_opts* o) {
 gp_status single_job(gp_graph* g, const gp_schedules* s, int32_t idx, CountJob* job) {
     gp_status rc = make_job(g, s, idx, nullptr, job);
     if (rc != GP_OK) return rc;
+    if (job->plan.labeled) return fail(GP_ERR_ARG, "labelled plans are counted by gp_count");
     return ensure_device(g);
 }
 
@@ -363,6 +368,41 @@ gp_status gp_pattern_create(const uint8_t* adj, int32_t k, gp_pattern** out) {
     return GP_OK;
 }
 
+gp_status gp_pattern_create_labeled(const uint8_t* adj, const int32_t* labels, int32_t k, gp_pattern** out) {
+    if (!adj || !labels || !out) return fail(GP_ERR_ARG, "null argument");
+    std::unique_ptr<gp_pattern> p(new (std::nothrow) gp_pattern());
+    if (!p) return fail(GP_ERR_NOMEM, "host allocation failed");
+    std::string err;
+    if (!pattern_init_labeled(p->info, adj, labels, k, err)) return fail(GP_ERR_PATTERN, err.c_str());
+    *out = p.release();
+    return GP_OK;
+}
+
+gp_status gp_graph_set_labels(gp_graph* g, const int32_t* labels, void* stream) {
+    if (!g || (!labels && g->n > 0)) return fail(GP_ERR_ARG, "null argument");
+    gp_status rc = ensure_device(g);
+    if (rc != GP_OK) return rc;
+    std::vector<int32_t> lab((size_t)g->n);
+    if (g->perm) {                            // labels arrive in the input labelling
+        std::vector<int32_t> perm((size_t)g->n);
+        GP_CUDA_TRY(cudaMemcpy(perm.data(), g->perm, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToHost));
+        for (int32_t i = 0; i < g->n; ++i) lab[i] = labels[perm[i]];
+    } else {
+        for (int32_t i = 0; i < g->n; ++i) lab[i] = labels[i];
+    }
+    int32_t* d = nullptr;
+    GP_CUDA_TRY(cudaMalloc(&d, sizeof(int32_t) * (size_t)(g->n ? g->n : 1)));
+    if (g->n) {
+        cudaError_t e = cudaMemcpyAsync(d, lab.data(), sizeof(int32_t) * (size_t)g->n, cudaMemcpyHostToDevice,
+                                        static_cast<cudaStream_t>(stream));
+        if (e == cudaSuccess) e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+        if (e != cudaSuccess) { cudaFree(d); set_error("label upload failed: %s", cudaGetErrorString(e)); return GP_ERR_CUDA; }
+    }
+    if (g->labels) cudaFree(g->labels);
+    g->labels = d;
+    return GP_OK;
+}
+
 gp_status gp_pattern_aut_count(const gp_pattern* p, uint64_t* out) {
     if (!p || !out) return fail(GP_ERR_ARG, "null argument");
     *out = p->info.auts.size();
@@ -521,6 +561,15 @@ gp_status gp_count(gp_graph* g, const gp_schedules* s, int32_t idx, const gp_cou
         return fail(GP_ERR_ARG, "inclusion-exclusion plans count whole graphs only (no task range or budget)");
     rc = ensure_device(g);
     if (rc != GP_OK) return rc;
+    if (job.plan.labeled) {                  // labelled plans: the listing kernel's counting pass
+        if (opts && opts->budget_cycles > 0) return fail(GP_ERR_ARG, "labelled counts take no budget");
+        int64_t w = 0, cut = 0, total = 0;
+        rc = run_list(job, nullptr, -1, static_cast<cudaStream_t>(stream), &w, &cut, &total);
+        if (rc != GP_OK) return rc;
+        if (opts && opts->resume_cursor) *opts->resume_cursor = job.task_begin + job.ntasks;
+        *out = (uint64_t)total;
+        return GP_OK;
+    }
     uint64_t res[2] = {0, 0};
     int64_t done = 0;
     float ms = 0.f;
@@ -561,6 +610,7 @@ gp_status gp_count_batch(gp_graph* const* graphs, const gp_schedules* const* sch
         r.split = opts ? opts->split : 0;
         gp_status rc = make_job(graphs[j], scheds[j], idx ? idx[j] : 0, &r, &jobs[j]);
         if (rc != GP_OK) return rc;
+        if (jobs[j].plan.labeled) return fail(GP_ERR_ARG, "labelled plans are counted by gp_count");
         if (graphs[j]->device != graphs[0]->device) return fail(GP_ERR_ARG, "graphs on different devices");
         jobs[j].task_offset = off;
         off += jobs[j].nvirt;
@@ -610,6 +660,7 @@ gp_status gp_count_batch_ranges(gp_graph* const* graphs, const gp_schedules* con
         gp_status rc = make_job(graphs[j], scheds[j], idx ? idx[j] : 0, &r, &jobs[j]);
         if (rc != GP_OK) return rc;
         if (jobs[j].plan.iep) return fail(GP_ERR_ARG, "inclusion-exclusion plans count whole graphs only");
+        if (jobs[j].plan.labeled) return fail(GP_ERR_ARG, "labelled plans are counted by gp_count");
         if (graphs[j]->device != graphs[0]->device) return fail(GP_ERR_ARG, "graphs on different devices");
         jobs[j].task_offset = off;
         off += jobs[j].nvirt;

@@ -111,6 +111,7 @@ struct TaskCtx {
     int lane_work;         // per-lane work limit before handing to the warp
     int* err;
     unsigned long long* sbytes;   // algorithmic-byte tally (instrumented kernel only)
+    const int32_t* labels; // vertex labels (labelled plans in the listing kernel)
     long long* deadline;   // this warp's current work-item deadline (shared memory; 0 = none)
     long long task_cycles; // work-item cycle limit (0 = none)
     int* job_abort;        // abort flag of the current job (global memory)
@@ -767,6 +768,7 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
     c.lane = lane;
     c.lane_work = lane_work;
     c.deadline = &s_deadline[w];
+    c.labels = nullptr;
     c.lane_bitmap = lane_bitmap == 1;
     const int bitmap_mode = lane_bitmap;    // 0 warp, 1 lane, 2 by pattern size
     c.task_cycles = task_cycles;
@@ -964,6 +966,7 @@ __device__ __forceinline__ int list_last(const TaskCtx& c, const int* v, int32_t
             x = __ldg(S.p + i);
             keep = true;
             for (int j = 0; j < L; ++j) keep &= !((lv.excl_mask >> j & 1) && v[j] == x);
+            if (P.labeled) keep &= __ldg(c.labels + x) == P.label[L];
         }
         const unsigned m = __ballot_sync(kFull, keep);
         if (write && keep) {
@@ -1014,6 +1017,7 @@ k_list(const CountJob* __restrict__ job, int64_t ntasks, unsigned long long* __r
     c.deadline = &s_deadline[w];
     c.task_cycles = 0;
     c.job_abort = err;
+    c.labels = job->labels;
     const GpPlan& P = s_plan[w];
     const int k = P.k;
     for (;;) {
@@ -1034,7 +1038,9 @@ k_list(const CountJob* __restrict__ job, int64_t ntasks, unsigned long long* __r
         v[1] = __ldg(c.col + e);
         int64_t found = 0;
         const int64_t at = kWrite ? per_task[t0] : 0;
-        const bool ok1 = !((P.lvl[1].lo_mask & 1) && !(v[1] > v[0])) && !((P.lvl[1].hi_mask & 1) && !(v[1] < v[0]));
+        bool ok1 = !((P.lvl[1].lo_mask & 1) && !(v[1] > v[0])) && !((P.lvl[1].hi_mask & 1) && !(v[1] < v[0]));
+        if (P.labeled)
+            ok1 = ok1 && __ldg(c.labels + v[0]) == P.label[0] && __ldg(c.labels + v[1]) == P.label[1];
         if (ok1) {
             run_builds(c, 1, v);
             if (k == 3) {
@@ -1053,6 +1059,7 @@ k_list(const CountJob* __restrict__ job, int64_t ntasks, unsigned long long* __r
                     const uint8_t ex = P.lvl[d].excl_mask;
                     bool skip = false;
                     for (int j = 0; j < d; ++j) skip |= ((ex >> j) & 1) && v[j] == x;
+                    if (P.labeled) skip |= __ldg(c.labels + x) != P.label[d];
                     if (skip) continue;
                     v[d] = x;
                     run_builds(c, d, v);
@@ -1312,10 +1319,12 @@ gp_status run_count_in_scratch(const CountJob* jobs, int njobs, void* d_scratch,
 }
 
 gp_status run_list(const CountJob& job, int32_t* d_out, int64_t capacity, cudaStream_t st,
-                   int64_t* n_written, int64_t* cut_tasks) {
+                   int64_t* n_written, int64_t* cut_tasks, int64_t* total) {
+    const bool count_only = capacity < 0;      // per-task counts and their sum only
     const int64_t T = job.ntasks;
     *n_written = 0;
     *cut_tasks = 0;
+    if (total) *total = 0;
     if (T == 0) return GP_OK;
     int dev = 0, nsm = 0, occ = 0;
     GP_CUDA_TRY(cudaGetDevice(&dev));
@@ -1349,7 +1358,7 @@ gp_status run_list(const CountJob& job, int32_t* d_out, int64_t capacity, cudaSt
     int64_t* counts = reinterpret_cast<int64_t*>(b + head_b + ((sizeof(CountJob) + 63) & ~(size_t)63));
     int64_t* offsets = counts + (T + 1);
     void* scan_tmp = offsets + (T + 1);
-    int64_t h[2] = {0, 0};
+    int64_t h[2] = {0, 0}, h_total = 0;
     int h_err = 0;
     cudaError_t e = cudaMemsetAsync(b, 0, head_b, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_job, &job, sizeof(CountJob), cudaMemcpyHostToDevice, st);
@@ -1362,13 +1371,14 @@ gp_status run_list(const CountJob& job, int32_t* d_out, int64_t capacity, cudaSt
     }
     if (e == cudaSuccess) e = cub::DeviceScan::ExclusiveSum(scan_tmp, scan_b, counts, offsets, T + 1, st);
     if (e == cudaSuccess) {
-        k_list_cut<<<1, 1, 0, st>>>(offsets, T, capacity, cut);
+        k_list_cut<<<1, 1, 0, st>>>(offsets, T, count_only ? 0 : capacity, cut);
         count_launch(2);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(h, cut, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_total, offsets + T, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e == cudaSuccess && h[0] > 0) {
+    if (e == cudaSuccess && h[0] > 0 && !count_only) {
         e = cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), st);
         if (e == cudaSuccess) {
             k_list<true><<<(unsigned)blocks, kWarps * 32, 0, st>>>(d_job, h[0], cursor, offsets, d_out, slots,
@@ -1385,6 +1395,7 @@ gp_status run_list(const CountJob& job, int32_t* d_out, int64_t capacity, cudaSt
     if (h_err) { set_error("listing kernel reported internal error %d", h_err); return GP_ERR_INTERNAL; }
     *cut_tasks = h[0];
     *n_written = h[1];
+    if (total) *total = h_total;
     return GP_OK;
 }
 

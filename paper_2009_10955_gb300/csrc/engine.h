@@ -21,6 +21,7 @@ struct gp_graph {
                                   // >= kHeavyDegree (degree-ordered graphs only)
     int64_t* row_ptr = nullptr;   // device, n + 1
     int32_t* col = nullptr;       // device, nnz
+    int32_t* labels = nullptr;      // device, n vertex labels (graph labelling) or null
     uint32_t* core_bits = nullptr;  // device, core_n x core_words: adjacency among
     int32_t core_n = 0;             // the core_n highest-degree vertices (ids
     int32_t core_words = 0;         // 0..core_n-1 of a degree-ordered graph)
@@ -64,6 +65,7 @@ struct CountJob {
     int32_t split;           // parts each of those tasks is cut into (>= 1)
     int32_t pad0;
     int64_t nvirt;           // work items: heavy * split + (ntasks - heavy)
+    const int32_t* labels;      // vertex labels (labelled plans), or null
     const uint32_t* core_bits;  // core adjacency bit matrix (null: none)
     int32_t core_n;
     int32_t core_words;
@@ -112,9 +114,10 @@ gp_status job_total(const CountJob& job, const uint64_t* res, uint64_t* out);
 
 // Listing: the embeddings of the longest prefix of the job's tasks whose
 // total fits `capacity` tuples, written to d_out (k int32 per embedding).
-// *cut_tasks receives that prefix's length, *n_written its embeddings.
+// *cut_tasks receives that prefix's length, *n_written its embeddings,
+// *total the embeddings of all the job's tasks. capacity < 0: count only.
 gp_status run_list(const CountJob& job, int32_t* d_out, int64_t capacity, cudaStream_t st,
-                   int64_t* n_written, int64_t* cut_tasks);
+                   int64_t* n_written, int64_t* cut_tasks, int64_t* total = nullptr);
 
 // Device scratch run_count would allocate for these jobs and options.
 gp_status scratch_bytes(const CountJob* jobs, int njobs, const LaunchOpts& lo, uint64_t* bytes);

@@ -60,5 +60,9 @@ struct GpPlan {
     // if v_1 is a core vertex the whole remaining search stays among core
     // vertices and runs on their adjacency bit matrix.
     int32_t core_dfs;
+    // vertex-labelled pattern: the vertex matched at depth d must carry
+    // label[d] (such plans run through the simple listing kernel)
+    int32_t labeled;
+    int32_t label[GP_MAX_K];
     GpLevel lvl[GP_MAX_K];
 };

@@ -106,6 +106,20 @@ bool pattern_init(PatternInfo& p, const uint8_t* adj, int k, std::string& err) {
     return true;
 }
 
+bool pattern_init_labeled(PatternInfo& p, const uint8_t* adj, const int32_t* labels, int k, std::string& err) {
+    if (!pattern_init(p, adj, k, err)) return false;
+    p.labeled = true;
+    for (int i = 0; i < k; ++i) p.labels[i] = labels[i];
+    std::vector<Perm> keep;
+    for (const Perm& q : p.auts) {
+        bool ok = true;
+        for (int a = 0; a < k && ok; ++a) ok = p.labels[q[a]] == p.labels[a];
+        if (ok) keep.push_back(q);
+    }
+    p.auts = keep;
+    return true;
+}
+
 bool no_conflict(const Perm& perm, ResMask res, int k) {
     uint8_t out[GP_MAX_K] = {};
     for (ResMask m = res; m; m &= m - 1) {
@@ -396,13 +410,15 @@ bool compile_plan(const PatternInfo& p, const int8_t* sched, ResMask res, GpPlan
         }
     }
     plan.nslots = nslots;
+    plan.labeled = p.labeled;
+    for (int d = 0; d < k; ++d) plan.label[d] = p.labeled ? p.labels[sched[d]] : -1;
     for (int x = 3; x < k; ++x) {
         const GpLevel& A = plan.lvl[x - 1];
         const GpLevel& B = plan.lvl[x];
         plan.lvl[x].bm_inc = B.op_mask == (uint8_t)(A.op_mask | (1u << (x - 1))) &&
                              (B.lo_mask & A.lo_mask) == A.lo_mask && (B.hi_mask & A.hi_mask) == A.hi_mask;
     }
-    plan.core_dfs = k >= 4;
+    plan.core_dfs = k >= 4 && !p.labeled;
     for (int x = 2; x < k; ++x)
         if (!gt[1][x]) plan.core_dfs = 0;      // some later vertex may exceed v_1
     *out = plan;

@@ -21,6 +21,8 @@ inline int res_bit(int a, int b) { return a * GP_MAX_K + b; }
 struct PatternInfo {
     int k = 0;
     uint8_t adj[GP_MAX_K][GP_MAX_K] = {};
+    bool labeled = false;
+    int32_t labels[GP_MAX_K] = {};   // vertex labels when labeled
     std::vector<Perm> auts;          // automorphism group (Section IV-A)
 
     std::mutex mu;                   // guards the lazily computed members below
@@ -35,6 +37,8 @@ struct PatternInfo {
 // Validates (3 <= k <= 7, symmetric 0/1, zero diagonal, connected) and
 // enumerates the automorphisms. Returns false with a message on bad input.
 bool pattern_init(PatternInfo& p, const uint8_t* adj, int k, std::string& err);
+// Same for a vertex-labelled pattern: automorphisms must also preserve labels.
+bool pattern_init_labeled(PatternInfo& p, const uint8_t* adj, const int32_t* labels, int k, std::string& err);
 
 // Algorithm 1 restriction sets (cached on the pattern). cap <= 0: default.
 const std::vector<ResMask>& restriction_sets(PatternInfo& p, int cap);

@@ -101,3 +101,13 @@ def test_explicit_schedule_validation(N):
     c4 = N.gp_pattern_create(named_pattern("c4"))
     with pytest.raises(N.GraphPiError):
         N.gp_schedule_explicit(c4, (0, 2, 1, 3), [(0, 1), (0, 2), (1, 3)])  # disconnected prefix
+
+
+@pytest.mark.parametrize("name,labels", [("house", [0, 0, 1, 1, 2]), ("house", [0, 1, 0, 1, 2]),
+                                         ("c4", [0, 1, 0, 1]), ("k4", [0, 0, 1, 1]), ("diamond", [1, 1, 0, 0])])
+def test_labeled_planner_matches_oracle(N, name, labels):
+    import oracle
+    adj = named_pattern(name)
+    p = N.gp_pattern_create_labeled(adj, labels)
+    assert p.aut_count() == len(pr.automorphisms(adj.tolist(), labels)) == oracle.aut_count_labeled(adj, labels)
+    assert set(p.restriction_sets()) == set(pr.restriction_sets(adj.tolist(), labels))

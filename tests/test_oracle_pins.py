@@ -365,3 +365,48 @@ def test_listing_is_the_set_of_embeddings():
         brute = {t for t in itertools.permutations(range(n), k)
                  if all(gadj[t[a], t[b]] for a, b in pe) and all(t[a] > t[b] for a, b in rs)}
         assert got == brute
+
+
+# ------------------------------------------------------------ labelled pins
+
+def test_labeled_uniform_labels_reduce_to_unlabeled():
+    n = 40
+    s, d = er_edges(n, 300, seed=8)
+    g = oracle.build_csr(n, s, d)
+    for name in ("house", "c4", "diamond"):
+        p = named_pattern(name)
+        k = p.shape[0]
+        assert oracle.count_labeled(p, [7] * k, g, [7] * n) == oracle.count(p, g)
+        assert oracle.aut_count_labeled(p, [7] * k) == oracle.aut_count(p)
+
+
+def test_labeled_alternating_cycle_in_bipartite():
+    # K_{a,b} with the two sides labelled 0 and 1: every 4-cycle alternates,
+    # so the 4-cycle labelled 0,1,0,1 has C(a,2) C(b,2) embeddings and the
+    # labelling 0,0,1,1 has none
+    for a, b in ((3, 4), (4, 5)):
+        g = bipartite(a, b)
+        gl = [0] * a + [1] * b
+        c4 = named_pattern("c4")
+        assert oracle.count_labeled(c4, [0, 1, 0, 1], g, gl) == math.comb(a, 2) * math.comb(b, 2)
+        assert oracle.count_labeled(c4, [0, 0, 1, 1], g, gl) == 0
+        assert oracle.aut_count_labeled(c4, [0, 1, 0, 1]) == 4
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_labeled_brute_force(seed):
+    n = 9
+    s, d = er_edges(n, 24, seed=seed)
+    g = oracle.build_csr(n, s, d)
+    gadj = dense(g)
+    gl = [(7 * v + seed) % 3 for v in range(n)]
+    for name, pl in (("triangle", [0, 1, 1]), ("house", [0, 0, 1, 2, 1]), ("path4", [2, 0, 0, 1])):
+        p = named_pattern(name)
+        k = p.shape[0]
+        pe = [(x, y) for x in range(k) for y in range(k) if p[x, y]]
+        maps = sum(1 for t in itertools.permutations(range(n), k)
+                   if all(gadj[t[x], t[y]] for x, y in pe) and all(gl[t[x]] == pl[x] for x in range(k)))
+        aut = sum(1 for q in itertools.permutations(range(k))
+                  if all(p[q[x], q[y]] for x, y in pe) and all(pl[q[x]] == pl[x] for x in range(k)))
+        assert oracle.aut_count_labeled(p, pl) == aut
+        assert oracle.count_labeled(p, pl, g, gl) == maps // aut
