@@ -68,8 +68,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU-baseline sample budget")
     ap.add_argument("--batched-graphs", default="rmat12,rmat11,rmat10,rmat9,rmat8",
                     help="candidate graphs of the batched comparison, largest first ('' to skip)")
-    ap.add_argument("--mode", default="count", choices=["count", "serve", "model"],
-                    help="serve: the continuous-batching sweep; model: performance-model accuracy")
+    ap.add_argument("--mode", default="count", choices=["count", "serve", "model", "case"],
+                    help="serve: the continuous-batching sweep; model: performance-model accuracy; "
+                         "case: one untimed count of each pattern on --graph (for profiler captures)")
+    ap.add_argument("--graph", default="rmat16", help="synthetic graph of --mode case")
     ap.add_argument("--model-graph", default="rmat14")
     ap.add_argument("--model-patterns", default="house,diamond,tailed_triangle,c4")
     ap.add_argument("--serve-scales", default="14,15,16,17,18,19,20,22")
@@ -212,6 +214,26 @@ def shard_range(ntasks, rank, world):
     return ntasks * rank // world, ntasks * (rank + 1) // world
 
 
+def shard_roots(row_ptr, rank, world):
+    """Contiguous root range [lo, hi) of one rank, cut so that every rank gets
+    about the same estimated work: a root of degree d owns d edge tasks of
+    about d steps each, so a range weighs the sum of its roots' d^2. The
+    ranges partition the roots; a rank's weight exceeds the mean by at most
+    one root's."""
+    rp = np.asarray(row_ptr, dtype=np.int64)
+    deg = np.diff(rp).astype(np.float64)
+    cum = np.concatenate([[0.0], np.cumsum(deg * deg)])
+    n = len(rp) - 1
+
+    def cut(r):
+        if r <= 0:
+            return 0
+        if r >= world:
+            return n
+        return min(n, int(np.searchsorted(cum, cum[-1] * r / world, side="left")))
+    return cut(rank), cut(rank + 1)
+
+
 def allreduce_counts(counts, device=None):
     """Exact sum over ranks of non-negative integer counts (< 2^64 each and in
     total): each count travels as two 32-bit halves in int64 lanes."""
@@ -270,8 +292,14 @@ def gpu_arm(a, rank, world):
         if a.iep:
             plans[p].set_iep(True)
         plan_s[p] = time.time() - t
-    # this rank's share of every pattern's edge tasks
-    lo, hi = shard_range(nnz, rank, world)
+    # this rank's share of every pattern's edge tasks: whole roots, balanced
+    # by the sum of squared degrees
+    if world > 1:
+        rp = g.csr()[0]
+        r0, r1 = shard_roots(rp, rank, world)
+        lo, hi = int(rp[r0]), int(rp[r1])
+    else:
+        lo, hi = 0, nnz
 
     # launch knobs per pattern from the autotuner (untimed, cached like plans)
     tuned, tune_s = {}, {}
@@ -630,6 +658,20 @@ def main():
             from paper_2009_10955_gb300 import native
             out = model_bench(native(), torch.cuda.current_stream(), a.model_graph, a.model_patterns.split(","))
             print(json.dumps(out), flush=True)
+        return
+    if a.mode == "case":
+        # graph (degree order), its triangle count for the performance model
+        # (the first count-kernel launch), then one count of each pattern
+        if rank == 0:
+            from paper_2009_10955_gb300 import native
+            N = native()
+            n, src, dst = workload_edges(a.graph)
+            g = N.gp_graph_create_edges(src, dst, n, N.GP_DEGREE_ORDER)
+            g.stats()
+            for pn in (a.patterns or "k4").split(","):
+                sc = N.gp_schedule(N.gp_pattern_create(named_pattern(pn)), g)
+                print(pn, N.gp_count(g, sc, 0), flush=True)
+            torch.cuda.synchronize()
         return
     if a.mode == "serve":
         if rank == 0:

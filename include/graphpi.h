@@ -244,10 +244,12 @@ typedef struct gp_count_opts {
                               (slower; for measurement only)                      */
 #define GP_COUNT_NO_CORE 2 /* never use the core adjacency bit matrix: every
                               membership test is a binary search                  */
-#define GP_COUNT_WARP_BITMAP 4 /* bitmap subtree: always count the last level one
+#define GP_COUNT_WARP_BITMAP 4 /* bitmap subtree: count the last level one
                               candidate at a time with the whole warp (default:
-                              one candidate per lane for patterns of 5 or more
-                              vertices, the whole warp for 4)                    */
+                              one candidate per lane)                             */
+#define GP_COUNT_LANE_BITMAP 8 /* bitmap subtree: one candidate per lane (the
+                              default; GP_COUNT_WARP_BITMAP wins when both are
+                              set)                                                */
 
 /* Count the embeddings of the pattern of `s` in `g` with plan `idx`.
  * Every embedding is counted exactly once (restrictions, Algorithm 1).

@@ -30,6 +30,7 @@ GP_ASSUME_CLEAN = 4
 GP_COUNT_STATS = 1
 GP_COUNT_NO_CORE = 2
 GP_COUNT_WARP_BITMAP = 4
+GP_COUNT_LANE_BITMAP = 8
 
 # Every function the header declares, with its ctypes signature.
 P = ctypes.c_void_p

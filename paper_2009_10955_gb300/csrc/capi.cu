@@ -174,7 +174,8 @@ LaunchOpts launch_opts(const gp_count_opts* o) {
         lo.stats = (o->flags & GP_COUNT_STATS) != 0;
         lo.no_core = (o->flags & GP_COUNT_NO_CORE) != 0;
         if (o->task_cycles > 0) lo.task_cycles = o->task_cycles;
-        lo.warp_bitmap = (o->flags & GP_COUNT_WARP_BITMAP) != 0;
+        if (o->flags & GP_COUNT_WARP_BITMAP) lo.bitmap_mode = 0;
+        else if (o->flags & GP_COUNT_LANE_BITMAP) lo.bitmap_mode = 1;
         if (o->lane_work > 0) lo.lane_work = o->lane_work;
     }
     return lo;

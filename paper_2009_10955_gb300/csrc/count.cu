@@ -552,51 +552,89 @@ __device__ __forceinline__ void bitmap_last_two(const TaskCtx& c, int* v, int W,
     }
     const bool any_excl = (lv.excl_mask & (uint8_t)((2u << d) - 1)) != 0;
     if (c.lane_bitmap) {
-        // one candidate per lane: lane b takes bit b of word w of S and scans
-        // its row with 16-byte loads over its window (rows and sets are
-        // padded to multiples of 4 words); for one word the windows end at
-        // almost the same place, so the lanes stay balanced
+        // one candidate per lane, the candidates ranked in increasing order:
+        // lane l owns words [l per, (l + 1) per) of S, a warp scan of their
+        // popcounts ranks every set bit, and each round hands the next 32
+        // ranks of this part to the 32 lanes, so that every lane but those of
+        // the last round has a candidate. Neighbouring ranks have similar
+        // windows, so the lanes' row scans (16-byte loads over the rows and
+        // sets, both padded to multiples of 4 words) stay balanced.
+        const int per = (Ws + 31) >> 5;
+        const int wb0 = min(Ws, c.lane * per), wb1 = min(Ws, wb0 + per);
+        int own = 0;
+        for (int w = wb0; w < wb1; ++w) own += __popc(S[w]);
+        int incl = own;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (c.lane >= o) incl += t;
+        }
+        const int T = __shfl_sync(kFull, incl, 31);
+        const int excl = incl - own;
+        const int np = (d == 2) ? nparts : 1, pt = (d == 2) ? part : 0;
+        const int J = (T > pt) ? (T - pt + np - 1) / np : 0;   // this part's candidates
         const uint4* PP4 = reinterpret_cast<const uint4*>(PP);
-        int ordinal_base = 0;
         unsigned long long mine_cnt = 0;
-        for (int w = 0; w < Ws; ++w) {
-            const uint32_t bw = S[w];
-            if (!bw) continue;
+        for (int j0 = 0; j0 < J; j0 += 32) {
             if (over(c)) return;
-            const int x = 32 * w + c.lane;
-            bool mine = (bw >> c.lane) & 1u;
-            if (d == 2 && nparts > 1) {
-                mine = mine && ((ordinal_base + __popc(bw & lanemask_lt())) % nparts) == part;
+            const int j = j0 + c.lane;
+            const int r = pt + np * min(j, J - 1);
+            int ol = 0;                               // lane owning rank r
+#pragma unroll
+            for (int st = 16; st; st >>= 1) {
+                const int e = __shfl_sync(kFull, excl, ol + st);
+                if (e <= r) ol += st;
             }
-            ordinal_base += __popc(bw);
-            if (!mine) continue;
+            const int owner_excl = __shfl_sync(kFull, excl, ol);
+            if (j >= J) continue;
+            int rem = r - owner_excl;
+            int w = ol * per;
+            uint32_t bw = S[w];
+            for (int pc = __popc(bw); rem >= pc; pc = __popc(bw)) { rem -= pc; bw = S[++w]; }
+            int pos = 0;                              // the rem-th set bit of bw
+#pragma unroll
+            for (int h = 16; h; h >>= 1) {
+                const int lowc = __popc(bw & ((1u << h) - 1u));
+                if (rem >= lowc) { rem -= lowc; bw >>= h; pos += h; }
+            }
+            const int x = 32 * w + pos;
             const int lo = x_lo ? max(base.lo, x) : base.lo;
             const int hi = x_hi ? min(base.hi, x) : base.hi;
             const int w0 = max(0, (lo + 1) >> 5);
             const int w1 = min(Wd, (hi == INT_MAX) ? Wd : ((hi + 31) >> 5));
             const uint4* rx4 = reinterpret_cast<const uint4*>(c.core_bits + (size_t)x * c.core_words);
-            unsigned long long cnt = 0;
-            for (int q = w0 >> 2; 4 * q < w1; ++q) {
-                const uint4 a = PP4[q];
-                const uint4 r = uses_x ? __ldg(rx4 + q) : make_uint4(~0u, ~0u, ~0u, ~0u);
-                const uint32_t aw[4] = {a.x & r.x, a.y & r.y, a.z & r.z, a.w & r.w};
+            int cnt = 0;
+            if (w0 < w1) {
+                const uint32_t m_first = window_bits(w0, lo, hi), m_last = window_bits(w1 - 1, lo, hi);
+                const int q0 = w0 >> 2, q1 = (w1 - 1) >> 2;
+                for (int q = q0; q <= q1; ++q) {
+                    const uint4 a = PP4[q];
+                    const uint4 rr = uses_x ? __ldg(rx4 + q) : make_uint4(~0u, ~0u, ~0u, ~0u);
+                    uint32_t m[4] = {a.x & rr.x, a.y & rr.y, a.z & rr.z, a.w & rr.w};
+                    if (q == q0 || q == q1) {         // words outside [w0, w1), partial end words
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int ww = 4 * q + t;
-                    if (ww >= w0 && ww < w1) cnt += __popc(aw[t] & window_bits(ww, lo, hi));
+                        for (int t = 0; t < 4; ++t) {
+                            const int ww = 4 * q + t;
+                            uint32_t keep = (ww < w0 || ww >= w1) ? 0u : ~0u;
+                            if (ww == w0) keep &= m_first;
+                            if (ww == w1 - 1) keep &= m_last;
+                            m[t] &= keep;
+                        }
+                    }
+                    cnt += __popc(m[0]) + __popc(m[1]) + __popc(m[2]) + __popc(m[3]);
                 }
             }
             if (any_excl) {
-                for (int j = 0; j <= d; ++j) {
-                    if (!(lv.excl_mask >> j & 1)) continue;
-                    const int y = (j == d) ? x : v[j];
+                for (int jj = 0; jj <= d; ++jj) {
+                    if (!(lv.excl_mask >> jj & 1)) continue;
+                    const int y = (jj == d) ? x : v[jj];
                     if (y <= lo || y >= hi || y >= 32 * Wd) continue;
                     bool in = (PP[y >> 5] >> (y & 31)) & 1u;
                     if (in && uses_x) in = (__ldg(c.core_bits + (size_t)x * c.core_words + (y >> 5)) >> (y & 31)) & 1u;
                     cnt -= in;
                 }
             }
-            mine_cnt += cnt;
+            mine_cnt += (unsigned)cnt;
         }
         acc.add(mine_cnt);
         return;
@@ -769,8 +807,8 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
     c.lane_work = lane_work;
     c.deadline = &s_deadline[w];
     c.labels = nullptr;
-    c.lane_bitmap = lane_bitmap == 1;
-    const int bitmap_mode = lane_bitmap;    // 0 warp, 1 lane, 2 by pattern size
+    c.lane_bitmap = lane_bitmap != 0;
+    const int bitmap_mode = lane_bitmap;    // 0 warp, 1 or 2 lane
     c.task_cycles = task_cycles;
     c.job_abort = aborts;
     if (lane == 0) s_deadline[w] = 0;
@@ -838,7 +876,7 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
                 c.core_n = (use_core && J.core_bits) ? J.core_n : 0;
                 // one candidate per lane pays off when the last level runs
                 // below two bitmap loops (k >= 5); 4-vertex plans prefer a warp
-                c.lane_bitmap = bitmap_mode == 1 || (bitmap_mode == 2 && J.plan.k >= 5);
+                c.lane_bitmap = bitmap_mode != 0;
                 if (c.core_n == 0 || J.core_words > c.bm_stride) c.bm = nullptr;
                 else if (bm_stride > 0 && !kStats && J.plan.k - 1 <= bm_sets)
                     c.bm = s_bitmaps + (size_t)w * bm_sets * bm_stride;
@@ -1220,7 +1258,7 @@ gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& opt, cuda
                                                       warp_elems, chunk, (long long)opt.budget_cycles,
                                                       d_err, d_stats, opt.lane_work > 0 ? opt.lane_work : kLaneWork,
                                                       opt.no_core ? 0 : 1, geo.bm_stride, geo.bm_sets,
-                                                      (long long)opt.task_cycles, d_aborts, opt.warp_bitmap ? 0 : 2);
+                                                      (long long)opt.task_cycles, d_aborts, opt.bitmap_mode);
         count_launch();
         e = cudaGetLastError();
     }

@@ -136,9 +136,9 @@ def test_every_configuration_agrees(N, pname):
 @pytest.mark.parametrize("gname", ["er:300:1500:5", "rmat10"])
 @pytest.mark.parametrize("pname", ["c4", "c5", "house", "diamond", "tailed_triangle", "k4", "path4", "k5"])
 def test_bitmap_paths_equal_list_path(N, gname, pname):
-    """Every sampled configuration: the core bit-matrix paths (one candidate
-    per lane, and one per warp) give the count of the pure list path, which
-    equals the oracle's."""
+    """Every sampled configuration: the core bit-matrix paths (default, one
+    candidate per warp, one candidate per lane) give the count of the pure
+    list path, which equals the oracle's."""
     g, ref = graph_pair(N, gname)
     adj = named_pattern(pname)
     p = N.gp_pattern_create(adj)
@@ -152,6 +152,7 @@ def test_bitmap_paths_equal_list_path(N, gname, pname):
         lists = N.gp_count(g, one, 0, N.make_opts(flags=N.GP_COUNT_NO_CORE))
         assert N.gp_count(g, one) == lists, (sc, r)
         assert N.gp_count(g, one, 0, N.make_opts(flags=N.GP_COUNT_WARP_BITMAP)) == lists, (sc, r)
+        assert N.gp_count(g, one, 0, N.make_opts(flags=N.GP_COUNT_LANE_BITMAP)) == lists, (sc, r)
         if expect is None:
             expect = lists
         assert lists == expect, (sc, r)
@@ -203,6 +204,8 @@ def test_partial_core_graph(N, pname):
     for split in (2, 8, 33):           # high-degree tasks cut into parts
         assert N.gp_count(g, s, 0, N.make_opts(split=split)) == got
         assert N.gp_count(g, s, 0, N.make_opts(split=split, flags=N.GP_COUNT_NO_CORE)) == got
+        for f in (N.GP_COUNT_LANE_BITMAP, N.GP_COUNT_WARP_BITMAP):
+            assert N.gp_count(g, s, 0, N.make_opts(split=split, flags=f)) == got
     if pname != "k5":
         assert got[1] == oracle.count_restricted(adj, order, res, ref)
     else:

@@ -29,7 +29,7 @@ def _rank_main(rank, world, port, q):
     n = 120
     s, d = er_edges(n, 900, seed=21)
     g = oracle.build_csr(n, s, d)
-    lo, hi = bench.shard_range(n, rank, world)           # rows of this rank
+    lo, hi = bench.shard_roots(g.row_ptr, rank, world)   # roots of this rank
     parts = []
     for name in ("triangle", "house", "c4"):
         adj = named_pattern(name)
@@ -71,3 +71,21 @@ def test_shard_ranges_partition():
             rs = [bench.shard_range(ntasks, r, world) for r in range(world)]
             assert rs[0][0] == 0 and rs[-1][1] == ntasks
             assert all(a[1] == b[0] for a, b in zip(rs, rs[1:]))
+
+
+def test_weighted_root_shards():
+    """Root shards partition the roots and balance the sum of squared
+    degrees to within one root."""
+    import bench
+    from synth import workload_edges
+    n, s, d = workload_edges("rmat12")
+    g = oracle.build_csr(n, s, d)
+    deg = np.diff(g.row_ptr).astype(np.float64)
+    w = deg * deg
+    for world in (1, 2, 3, 8):
+        rs = [bench.shard_roots(g.row_ptr, r, world) for r in range(world)]
+        assert rs[0][0] == 0 and rs[-1][1] == n
+        assert all(a[1] == b[0] and a[0] <= a[1] for a, b in zip(rs, rs[1:]))
+        for lo, hi in rs:
+            assert w[lo:hi].sum() <= w.sum() / world + w.max()
+    assert bench.shard_roots(np.zeros(1, np.int64), 0, 2) == (0, 0)
