@@ -246,10 +246,12 @@ typedef struct gp_count_opts {
                               membership test is a binary search                  */
 #define GP_COUNT_WARP_BITMAP 4 /* bitmap subtree: count the last level one
                               candidate at a time with the whole warp (default:
-                              one candidate per lane)                             */
-#define GP_COUNT_LANE_BITMAP 8 /* bitmap subtree: one candidate per lane (the
-                              default; GP_COUNT_WARP_BITMAP wins when both are
-                              set)                                                */
+                              one candidate per lane, and for plans whose last
+                              two sets are incremental one candidate of depth
+                              k-3 per lane running the last three levels)         */
+#define GP_COUNT_LANE_BITMAP 8 /* bitmap subtree: one candidate per lane for the
+                              last two levels only (GP_COUNT_WARP_BITMAP wins
+                              when both are set)                                  */
 
 /* Count the embeddings of the pattern of `s` in `g` with plan `idx`.
  * Every embedding is counted exactly once (restrictions, Algorithm 1).

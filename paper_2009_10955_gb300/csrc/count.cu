@@ -107,6 +107,7 @@ struct TaskCtx {
     uint32_t* bm;          // this warp's bitmap sets (shared memory) or null
     int bm_stride;         // words per bitmap set
     bool lane_bitmap;      // bitmap last level: one candidate per lane
+    bool lane_three;       // bitmap last three levels: one candidate per lane where the plan allows
     int lane;
     int lane_work;         // per-lane work limit before handing to the warp
     int* err;
@@ -675,6 +676,146 @@ __device__ __forceinline__ void bitmap_last_two(const TaskCtx& c, int* v, int W,
     }
 }
 
+// Rank of a set bit of S (Ws words) for one lane, shared by the lane paths:
+// lane l owns words [l per, (l + 1) per); `excl` is the number of set bits
+// in the words of lanes below l, `T` the total.
+struct RankScan {
+    int per, excl, T;
+};
+
+__device__ __forceinline__ RankScan rank_scan(const TaskCtx& c, const uint32_t* S, int Ws) {
+    RankScan r;
+    r.per = (Ws + 31) >> 5;
+    const int wb0 = min(Ws, c.lane * r.per), wb1 = min(Ws, wb0 + r.per);
+    int own = 0;
+    for (int w = wb0; w < wb1; ++w) own += __popc(S[w]);
+    int incl = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, incl, o);
+        if (c.lane >= o) incl += t;
+    }
+    r.T = __shfl_sync(kFull, incl, 31);
+    r.excl = incl - own;
+    return r;
+}
+
+// The set bit of rank r (0-based) of S. Called by every lane (r may differ).
+__device__ __forceinline__ int rank_select(const uint32_t* S, const RankScan& rs, int r) {
+    int ol = 0;                               // lane owning rank r
+#pragma unroll
+    for (int st = 16; st; st >>= 1) {
+        const int e = __shfl_sync(kFull, rs.excl, ol + st);
+        if (e <= r) ol += st;
+    }
+    int rem = r - __shfl_sync(kFull, rs.excl, ol);
+    int w = ol * rs.per;
+    uint32_t bw = S[w];
+    for (int pc = __popc(bw); rem >= pc; pc = __popc(bw)) { rem -= pc; bw = S[++w]; }
+    int pos = 0;                              // the rem-th set bit of bw
+#pragma unroll
+    for (int h = 16; h; h >>= 1) {
+        const int lowc = __popc(bw & ((1u << h) - 1u));
+        if (rem >= lowc) { rem -= lowc; bw >>= h; pos += h; }
+    }
+    return 32 * w + pos;
+}
+
+// The last three levels with one candidate of depth d = k-3 per lane, for
+// plans whose last two levels are built incrementally (each is the set
+// before it AND the row of the vertex bound before it, inside a window no
+// wider than the one before). Lane-held x = v_d walks the set of depth k-2,
+// S_d AND row(x) inside that level's window; for each member y it counts the
+// last level's set, S_d AND row(x) AND row(y) inside its window. Matched
+// vertices v_j (j < d) are removed from both sets where they lie inside
+// them (x and y are never in their own rows). One round of the warp hands
+// the next 32 candidates of this part to the lanes; each lane then runs its
+// candidate's whole subtree without further warp-wide steps.
+__device__ __noinline__ void bitmap_last_three(const TaskCtx& c, int* v, int Ws, Acc& acc, int part,
+                                                  int nparts) {
+    const GpPlan& P = *c.P;
+    const int d = P.k - 3, e = P.k - 2;
+    const GpLevel& le = P.lvl[e];
+    const GpLevel& lL = P.lvl[P.k - 1];
+    const uint32_t* S = c.bm + (size_t)d * c.bm_stride;
+    const uint8_t xb = (uint8_t)(1u << d), yb = (uint8_t)(1u << e);
+    const Window be = window(le.lo_mask & (uint8_t)~xb, le.hi_mask & (uint8_t)~xb, v);
+    const Window bL = window(lL.lo_mask & (uint8_t)~(xb | yb), lL.hi_mask & (uint8_t)~(xb | yb), v);
+    const bool e_xlo = le.lo_mask & xb, e_xhi = le.hi_mask & xb;
+    const bool L_xlo = lL.lo_mask & xb, L_xhi = lL.hi_mask & xb;
+    const bool L_ylo = lL.lo_mask & yb, L_yhi = lL.hi_mask & yb;
+    const uint8_t below = (uint8_t)((1u << d) - 1u);
+    const uint8_t ex_e = le.excl_mask & below, ex_L = (uint8_t)((le.excl_mask | lL.excl_mask) & below);
+    const RankScan rs = rank_scan(c, S, Ws);
+    const int np = (d == 2) ? nparts : 1, pt = (d == 2) ? part : 0;
+    const int J = (rs.T > pt) ? (rs.T - pt + np - 1) / np : 0;
+    const uint4* S4 = reinterpret_cast<const uint4*>(S);
+    unsigned long long mine = 0;
+    for (int j0 = 0; j0 < J; j0 += 32) {
+        if (over(c)) return;
+        const int j = j0 + c.lane;
+        const int x = rank_select(S, rs, pt + np * min(j, J - 1));
+        if (j >= J) continue;
+        const uint32_t* rx = c.core_bits + (size_t)x * c.core_words;
+        const uint4* rx4 = reinterpret_cast<const uint4*>(rx);
+        const int lo_e = e_xlo ? max(be.lo, x) : be.lo;
+        const int hi_e = e_xhi ? min(be.hi, x) : be.hi;
+        const int we0 = max(0, (lo_e + 1) >> 5);
+        const int we1 = min(Ws, (hi_e == INT_MAX) ? Ws : ((hi_e + 31) >> 5));
+        for (int w = we0; w < we1; ++w) {
+            uint32_t m = S[w] & __ldg(rx + w);
+            if (w == we0 || w == we1 - 1) m &= window_bits(w, lo_e, hi_e);
+            while (m) {
+                const int y = 32 * w + __ffs(m) - 1;
+                m &= m - 1;
+                bool skip = false;
+                for (int jj = 0; jj < d; ++jj) skip |= ((ex_e >> jj) & 1) && v[jj] == y;
+                if (skip) continue;
+                int lo = bL.lo, hi = bL.hi;
+                if (L_xlo) lo = max(lo, x);
+                if (L_ylo) lo = max(lo, y);
+                if (L_xhi) hi = min(hi, x);
+                if (L_yhi) hi = min(hi, y);
+                const int w0 = max(0, (lo + 1) >> 5);
+                const int w1 = min(Ws, (hi == INT_MAX) ? Ws : ((hi + 31) >> 5));
+                const uint32_t* ry = c.core_bits + (size_t)y * c.core_words;
+                const uint4* ry4 = reinterpret_cast<const uint4*>(ry);
+                int cnt = 0;
+                if (w0 < w1) {
+                    const uint32_t m_first = window_bits(w0, lo, hi), m_last = window_bits(w1 - 1, lo, hi);
+                    const int q0 = w0 >> 2, q1 = (w1 - 1) >> 2;
+                    for (int q = q0; q <= q1; ++q) {
+                        const uint4 a = S4[q], b = __ldg(rx4 + q), f = __ldg(ry4 + q);
+                        uint32_t t4[4] = {a.x & b.x & f.x, a.y & b.y & f.y, a.z & b.z & f.z, a.w & b.w & f.w};
+                        if (q == q0 || q == q1) {
+#pragma unroll
+                            for (int t = 0; t < 4; ++t) {
+                                const int ww = 4 * q + t;
+                                uint32_t keep = (ww < w0 || ww >= w1) ? 0u : ~0u;
+                                if (ww == w0) keep &= m_first;
+                                if (ww == w1 - 1) keep &= m_last;
+                                t4[t] &= keep;
+                            }
+                        }
+                        cnt += __popc(t4[0]) + __popc(t4[1]) + __popc(t4[2]) + __popc(t4[3]);
+                    }
+                }
+                if (ex_L) {
+                    for (int jj = 0; jj < d; ++jj) {
+                        if (!((ex_L >> jj) & 1)) continue;
+                        const int u = v[jj];
+                        if (u <= lo || u >= hi || u >= 32 * Ws) continue;
+                        const int uw = u >> 5;
+                        cnt -= (int)((S[uw] & __ldg(rx + uw) & __ldg(ry + uw)) >> (u & 31) & 1u);
+                    }
+                }
+                mine += (unsigned)cnt;
+            }
+        }
+    }
+    acc.add(mine);
+}
+
 __device__ void bitmap_task(const TaskCtx& c, int* v, Acc& acc, int part, int nparts) {
     const GpPlan& P = *c.P;
     const int k = P.k;
@@ -696,10 +837,17 @@ __device__ void bitmap_task(const TaskCtx& c, int* v, Acc& acc, int part, int np
         bitmap_last_two(c, v, W, W2, n0_smem, acc, part, nparts);
         return;
     }
+    // the last three levels one candidate per lane when the last two sets
+    // are incremental (clique-like tails)
+    const bool three = c.lane_three && P.lvl[k - 2].bm_inc && P.lvl[k - 1].bm_inc;
     int word[GP_MAX_K], Wd[GP_MAX_K];
     uint32_t bits[GP_MAX_K];
     int d = 2, ordinal2 = 0;
     Wd[2] = bitmap_build(c, v, 2, W, W, n0_smem);
+    if (three && k == 5) {
+        bitmap_last_three(c, v, Wd[2], acc, part, nparts);
+        return;
+    }
     word[2] = -1;
     bits[2] = 0;
     while (d >= 2) {
@@ -709,7 +857,9 @@ __device__ void bitmap_task(const TaskCtx& c, int* v, Acc& acc, int part, int np
         if (d == 2 && (ordinal2++ % nparts) != part) continue;  // another part's candidate
         v[d] = x;
         Wd[d + 1] = bitmap_build(c, v, d + 1, W, Wd[d], n0_smem);
-        if (d + 1 == k - 2) {
+        if (three && d + 1 == k - 3) {
+            bitmap_last_three(c, v, Wd[d + 1], acc, 0, 1);
+        } else if (d + 1 == k - 2) {
             bitmap_last_two(c, v, W, Wd[d + 1], n0_smem, acc, 0, 1);
         } else {
             ++d;
@@ -808,7 +958,8 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
     c.deadline = &s_deadline[w];
     c.labels = nullptr;
     c.lane_bitmap = lane_bitmap != 0;
-    const int bitmap_mode = lane_bitmap;    // 0 warp, 1 or 2 lane
+    c.lane_three = lane_bitmap == 2;
+    const int bitmap_mode = lane_bitmap;    // 0 warp, 1 lane (last two levels), 2 lane (last three where allowed)
     c.task_cycles = task_cycles;
     c.job_abort = aborts;
     if (lane == 0) s_deadline[w] = 0;
@@ -877,6 +1028,7 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
                 // one candidate per lane pays off when the last level runs
                 // below two bitmap loops (k >= 5); 4-vertex plans prefer a warp
                 c.lane_bitmap = bitmap_mode != 0;
+                c.lane_three = bitmap_mode == 2;
                 if (c.core_n == 0 || J.core_words > c.bm_stride) c.bm = nullptr;
                 else if (bm_stride > 0 && !kStats && J.plan.k - 1 <= bm_sets)
                     c.bm = s_bitmaps + (size_t)w * bm_sets * bm_stride;
@@ -1048,6 +1200,7 @@ k_list(const CountJob* __restrict__ job, int64_t ntasks, unsigned long long* __r
     c.bm = nullptr;
     c.bm_stride = 0;
     c.lane_bitmap = false;
+    c.lane_three = false;
     c.lane = lane;
     c.lane_work = kLaneWork;
     c.err = err;

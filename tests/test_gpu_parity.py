@@ -134,11 +134,13 @@ def test_every_configuration_agrees(N, pname):
 
 
 @pytest.mark.parametrize("gname", ["er:300:1500:5", "rmat10"])
-@pytest.mark.parametrize("pname", ["c4", "c5", "house", "diamond", "tailed_triangle", "k4", "path4", "k5"])
+@pytest.mark.parametrize("pname", ["c4", "c5", "house", "diamond", "tailed_triangle", "k4", "path4", "k5",
+                                   "k6e", "k6", "k7"])
 def test_bitmap_paths_equal_list_path(N, gname, pname):
-    """Every sampled configuration: the core bit-matrix paths (default, one
-    candidate per warp, one candidate per lane) give the count of the pure
-    list path, which equals the oracle's."""
+    """Every sampled configuration: the core bit-matrix paths (default, with
+    the three-level lane tail where the plan allows it; one candidate per
+    warp; one candidate per lane for the last two levels) give the count of
+    the pure list path, which equals the oracle's."""
     g, ref = graph_pair(N, gname)
     adj = named_pattern(pname)
     p = N.gp_pattern_create(adj)
