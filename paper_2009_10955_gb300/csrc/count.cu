@@ -731,7 +731,7 @@ __device__ __forceinline__ int rank_select(const uint32_t* S, const RankScan& rs
 // them (x and y are never in their own rows). One round of the warp hands
 // the next 32 candidates of this part to the lanes; each lane then runs its
 // candidate's whole subtree without further warp-wide steps.
-__device__ __noinline__ void bitmap_last_three(const TaskCtx& c, int* v, int Ws, Acc& acc, int part,
+__device__ __forceinline__ void bitmap_last_three(const TaskCtx& c, int* v, int Ws, Acc& acc, int part,
                                                   int nparts) {
     const GpPlan& P = *c.P;
     const int d = P.k - 3, e = P.k - 2;
