@@ -768,9 +768,11 @@ __device__ __forceinline__ void bitmap_last_three(const TaskCtx& c, int* v, int 
             while (m) {
                 const int y = 32 * w + __ffs(m) - 1;
                 m &= m - 1;
-                bool skip = false;
-                for (int jj = 0; jj < d; ++jj) skip |= ((ex_e >> jj) & 1) && v[jj] == y;
-                if (skip) continue;
+                if (ex_e) {
+                    bool skip = false;
+                    for (int jj = 0; jj < d; ++jj) skip |= ((ex_e >> jj) & 1) && v[jj] == y;
+                    if (skip) continue;
+                }
                 int lo = bL.lo, hi = bL.hi;
                 if (L_xlo) lo = max(lo, x);
                 if (L_ylo) lo = max(lo, y);
