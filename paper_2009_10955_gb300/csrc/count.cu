@@ -1318,11 +1318,22 @@ gp_status geometry(const CountJob* jobs, int njobs, const LaunchOpts& opt, Geome
     GP_CUDA_TRY(cudaGetDevice(&dev));
     GP_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     int occ = 0;
-    // three register budgets: 64 registers (4 blocks per SM, the default: the
-    // kernel is latency-bound and gains more from warps than from registers),
-    // 85 (3 blocks per SM) or about 100 (2 blocks per SM), chosen by the
-    // requested blocks per SM
-    const int want = opt.blocks_per_sm;
+    // three register budgets, chosen by the requested blocks per SM: 64
+    // registers (4 blocks), 80 (3 blocks) or the compiler's choice (1 or 2).
+    // Default: 3 blocks when some job runs the three-level lane tail of the
+    // bitmap subtree, whose loop nest spills at 64 registers; otherwise 4
+    // (the kernel is latency-bound and gains more from warps than from
+    // registers)
+    int want = opt.blocks_per_sm;
+    if (want <= 0) {
+        want = 4;
+        if (!opt.stats && !opt.no_core && opt.bitmap_mode == 2)
+            for (int j = 0; j < njobs; ++j) {
+                const GpPlan& P = jobs[j].plan;
+                if (P.core_dfs && jobs[j].core_bits && P.k >= 5 && P.lvl[P.k - 2].bm_inc && P.lvl[P.k - 1].bm_inc)
+                    want = 3;
+            }
+    }
     if (want == 1 || want == 2) g->kern = opt.stats ? k_count<true, 1> : k_count<false, 1>;
     else if (want == 3) g->kern = opt.stats ? k_count<true, 3> : k_count<false, 3>;
     else g->kern = opt.stats ? k_count<true, 4> : k_count<false, 4>;
@@ -1339,7 +1350,7 @@ gp_status geometry(const CountJob* jobs, int njobs, const LaunchOpts& opt, Geome
     if (g->smem > 48 * 1024)
         GP_CUDA_TRY(cudaFuncSetAttribute(g->kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem));
     GP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, g->kern, kWarps * 32, g->smem));
-    int per_sm = opt.blocks_per_sm > 0 ? std::min(opt.blocks_per_sm, occ) : occ;
+    int per_sm = std::min(want, occ);
     if (per_sm < 1) per_sm = 1;
     g->blocks = (int64_t)nsm * per_sm;
     size_t free_b = 0, total_b = 0;
