@@ -104,6 +104,7 @@ class ClockSampler:
     def __init__(self, uuid):
         self.rows = []
         self.proc = None
+        self.uuid = uuid
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", uuid, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
@@ -128,14 +129,30 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         rows = self.rows
+        note = None
+        if not rows:
+            # timed region shorter than the 200 ms sampling period: one query
+            # right after it, while the clocks still reflect the load
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", self.uuid, f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=10).stdout
+                rows = [[x.strip() for x in line.split(",")] for line in out.splitlines()]
+                rows = [r for r in rows if len(r) == 8]
+                note = "timed region shorter than the sampling period; sampled right after it"
+            except Exception:
+                rows = []
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
         mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+        out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+               "reasons": reasons, "samples": len(rows)}
+        if note:
+            out["note"] = note
+        return out
 
 
 # -------------------------------------------------------------- CPU baseline
