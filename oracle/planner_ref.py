@@ -217,3 +217,51 @@ def all_configurations(adj, n_vertices, n_edges, tri_cnt):
     rows = [(cost(adj, s, r, n_vertices, n_edges, tri_cnt), s, r) for s in scheds for r in sets]
     rows.sort()
     return rows
+
+
+def components(k, pairs):
+    """Connected components of the undirected graph on vertices 1..k whose
+    edges are `pairs` (Algorithm 2's partition step), each a sorted list,
+    ordered by smallest member."""
+    parent = list(range(k + 1))
+
+    def find(a):
+        while parent[a] != a:
+            a = parent[a]
+        return a
+    for i, j in pairs:
+        ri, rj = find(i), find(j)
+        if ri != rj:
+            parent[max(ri, rj)] = min(ri, rj)
+    comps = {}
+    for v in range(1, k + 1):
+        comps.setdefault(find(v), []).append(v)
+    return sorted(comps.values())
+
+
+def intersection_card(k, pairs, sets):
+    """Algorithm 2: |A_{i1,j1} ∩ ... ∩ A_{im,jm}|, the number of tuples with
+    e_l in S_l for every l and e_i = e_j for every listed pair. Each connected
+    component of the pairs must take one common value from the intersection of
+    its sets; the components choose independently. `sets[l - 1]` is S_l."""
+    card = 1
+    for comp in components(k, pairs):
+        common = set(sets[comp[0] - 1])
+        for v in comp[1:]:
+            common &= set(sets[v - 1])
+        card *= len(common)
+    return card
+
+
+def iep_count(sets):
+    """|S_IEP| of Section IV-D: tuples (e_1, ..., e_k), e_l in S_l, with
+    pairwise distinct entries, by inclusion-exclusion over every subset of
+    the pairs (i, j), i < j, each term from Algorithm 2."""
+    k = len(sets)
+    all_pairs = [(i, j) for i in range(1, k + 1) for j in range(i + 1, k + 1)]
+    total = 0
+    for m in range(len(all_pairs) + 1):
+        for sub in combinations(all_pairs, m):
+            total += (-1) ** m * intersection_card(k, sub, sets)
+    return total
+
