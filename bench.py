@@ -653,10 +653,11 @@ def reference_arm(a):
             vals.append(cb["value"])
     v = statistics.mean(vals)
     cb["value"] = v
-    return {"metric": "pattern-count time (s)", "value": v, "unit": "s", "n_gpus": 0, "steps": a.steps,
+    return {"metric": "pattern-count time (s)", "value": v, "unit": "s", "n_gpus": a.gpus, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": v * 1000.0, "higher_is_better": False, "impl": "reference",
             "scaling": "strong", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": a.workload, "graph": wl["graph"], "patterns": pats},
+            "devices": "host cores only (the oracle runs on the CPU; rank 0 alone)",
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
