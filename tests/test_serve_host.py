@@ -1,0 +1,181 @@
+"""The serving loop's host logic on CPU, with a fake of the library: partial
+counts over time slices add up exactly, admission respects the memory
+budget, and every failure path (a work item over its limit, too many
+slices, a planning error, a failing launch) answers the affected requests
+with an error while the others complete. No GPU: the fake stands in for
+gp_count_batch_ranges and the planner calls."""
+
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_2009_10955_gb300 import serve
+
+
+class FakeGraph:
+    def __init__(self, nnz):
+        self.nnz = nnz
+
+    def device_csr(self):
+        return 0, 0, self.nnz
+
+
+class FakeSched:
+    def __init__(self, adj):
+        self.k = adj.shape[0]
+        self.key = adj.tobytes()
+
+
+class FakeNative:
+    """Each slice advances every job by `per_slice` tasks; a task of a
+    k-vertex pattern counts k. A pattern with a self loop fails planning; a
+    job whose task range reaches `poison_task` is abandoned (next = -1)."""
+
+    def __init__(self, per_slice=7, poison_task=None, fail_launch=False):
+        self.per_slice = per_slice
+        self.poison_task = poison_task
+        self.fail_launch = fail_launch
+        self.max_batch_seen = 0
+        self.launches = 0
+        self.lock = threading.Lock()
+
+    def gp_pattern_create(self, adj):
+        if np.any(np.diag(adj)):
+            raise ValueError("bad pattern")
+        return adj
+
+    def gp_schedule(self, pattern, graph, top_k=1, stream=None):
+        return FakeSched(pattern)
+
+    def gp_count_scratch_bytes(self, graph, sched, idx):
+        return 1000 * sched.k
+
+    def make_opts(self, **kw):
+        return kw
+
+    def gp_count_batch_ranges(self, graphs, scheds, idx, begin, end, opts, stream=None):
+        with self.lock:
+            self.launches += 1
+            self.max_batch_seen = max(self.max_batch_seen, len(graphs))
+        if self.fail_launch:
+            raise RuntimeError("launch failed")
+        out, nxt = [], []
+        for s, b, e in zip(scheds, begin, end):
+            t = min(e, b + self.per_slice)
+            if self.poison_task is not None and b <= self.poison_task < t and s.k == 5:
+                out.append(0)
+                nxt.append(-1)
+                continue
+            out.append((t - b) * s.k)
+            nxt.append(t)
+        return 0, np.array(out, np.uint64), np.array(nxt, np.int64)
+
+
+def adj_k(k):
+    a = np.ones((k, k), np.uint8)
+    np.fill_diagonal(a, 0)
+    return a
+
+
+@pytest.fixture
+def fake(monkeypatch):
+    def make(**kw):
+        f = FakeNative(**kw)
+        monkeypatch.setattr(serve, "N", f)
+        return f
+    return make
+
+
+def wait_all(reqs, timeout=10.0):
+    for r in reqs:
+        assert r.done.wait(timeout), f"request {r.rid} did not finish"
+
+
+def test_slices_add_up_exactly(fake):
+    f = fake(per_slice=7)
+    srv = serve.Server({"a": FakeGraph(100), "b": FakeGraph(31)}, slice_ms=1.0)
+    try:
+        reqs = [srv.submit("a", adj_k(3)), srv.submit("b", adj_k(4)), srv.submit("a", adj_k(4))]
+        wait_all(reqs)
+    finally:
+        srv.close()
+    assert [r.count for r in reqs] == [300, 124, 400]
+    assert [r.error for r in reqs] == [None, None, None]
+    assert reqs[0].slices == 15 and reqs[1].slices == 5      # ceil(100 / 7), ceil(31 / 7)
+    assert f.max_batch_seen >= 2                             # the jobs shared launches
+
+
+def test_memory_budget_limits_the_batch(fake):
+    f = fake(per_slice=5)
+    # scratch 1000 k bytes per job; a budget of 3500 admits one 3-vertex job
+    # beside nothing larger than itself at a time
+    srv = serve.Server({"a": FakeGraph(40)}, slice_ms=1.0, mem_budget=3500)
+    try:
+        reqs = [srv.submit("a", adj_k(3)) for _ in range(2)] + [srv.submit("a", adj_k(4))]
+        wait_all(reqs)
+    finally:
+        srv.close()
+    assert [r.count for r in reqs] == [120, 120, 160]
+    assert f.max_batch_seen == 2         # two 3-vertex jobs fit; the 4-vertex job waits
+
+
+def test_abandoned_work_item_times_out_alone(fake):
+    fake(per_slice=10, poison_task=25)
+    srv = serve.Server({"a": FakeGraph(60)}, slice_ms=1.0, item_ms=1.0)
+    try:
+        bad = srv.submit("a", adj_k(5))
+        good = srv.submit("a", adj_k(3))
+        wait_all([bad, good])
+    finally:
+        srv.close()
+    assert isinstance(bad.error, TimeoutError) and bad.count is None
+    assert good.error is None and good.count == 180
+
+
+def test_max_slices_and_deadline(fake):
+    fake(per_slice=1)
+    srv = serve.Server({"a": FakeGraph(50)}, slice_ms=1.0, max_slices=3)
+    try:
+        r = srv.submit("a", adj_k(3))
+        wait_all([r])
+    finally:
+        srv.close()
+    assert isinstance(r.error, TimeoutError) and r.slices == 3
+    fake(per_slice=1)
+    srv = serve.Server({"a": FakeGraph(10 ** 9)}, slice_ms=1.0, deadline_s=0.05)
+    try:
+        r = srv.submit("a", adj_k(3))
+        wait_all([r])
+    finally:
+        srv.close()
+    assert isinstance(r.error, TimeoutError) and r.latency >= 0.05
+
+
+def test_planning_error_answers_only_that_request(fake):
+    fake(per_slice=50)
+    srv = serve.Server({"a": FakeGraph(20)}, slice_ms=1.0)
+    bad_adj = adj_k(3)
+    bad_adj[0, 0] = 1
+    try:
+        bad = srv.submit("a", bad_adj)
+        good = srv.submit("a", adj_k(3))
+        wait_all([bad, good])
+    finally:
+        srv.close()
+    assert isinstance(bad.error, ValueError)
+    assert good.count == 60
+
+
+def test_failing_launch_answers_the_batch(fake):
+    fake(fail_launch=True)
+    srv = serve.Server({"a": FakeGraph(20)}, slice_ms=1.0)
+    try:
+        reqs = [srv.submit("a", adj_k(3)), srv.submit("a", adj_k(4))]
+        wait_all(reqs)
+        # the server keeps serving after a failed launch
+        assert srv.thread.is_alive()
+    finally:
+        srv.close()
+    assert all(isinstance(r.error, RuntimeError) for r in reqs)
