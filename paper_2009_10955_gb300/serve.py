@@ -10,6 +10,14 @@ admitted as long as the slice's intermediate-set scratch stays within the
 memory budget. A job's partial counts over disjoint task ranges add up to
 its exact count, so a job may span any number of slices.
 
+The launch hands out the jobs' edge tasks in job order, so a job with
+expensive tasks at the front of the order could take a whole slice from the
+jobs behind it. Each job therefore gets a task window per slice (its quota):
+the quota doubles while the job finishes its window inside the slice and
+halves below what the job managed when the slice ended first (leaving the
+rest of the next slice to the others); and the job order rotates from slice
+to slice, so that every job is at the front in turn.
+
 The scheduling here is host-side bookkeeping; all counting runs in the
 library's kernels.
 """
@@ -23,9 +31,21 @@ import numpy as np
 from . import _native as N
 
 
+def next_quota(quota, done, finished_window, quota_min):
+    """Task window of a job for its next slice: double it after a window
+    the job finished inside the slice, half of what it managed when the
+    slice ended first, unchanged when it made no progress (it was behind
+    other jobs; the rotation brings it forward)."""
+    if finished_window:
+        return min(2 * quota, 1 << 40)
+    if done > 0:
+        return max(quota_min, done // 2)
+    return quota
+
+
 class Request:
     __slots__ = ("rid", "graph", "adj", "arrival", "done", "count", "error", "finish", "sched",
-                 "next_task", "end_task", "acc", "slices", "scratch")
+                 "next_task", "end_task", "acc", "slices", "scratch", "quota")
 
     def __init__(self, rid, graph, adj, arrival):
         self.rid = rid
@@ -42,6 +62,7 @@ class Request:
         self.acc = 0
         self.slices = 0
         self.scratch = 0
+        self.quota = 0
 
     @property
     def latency(self):
@@ -52,7 +73,8 @@ class Server:
     """Continuous batching over device-resident graphs (see module doc)."""
 
     def __init__(self, graphs, slice_ms=20.0, max_batch=256, mem_budget=None, stream=None,
-                 clock_ghz=1.9, max_slices=None, item_ms=None, deadline_s=None):
+                 clock_ghz=1.9, max_slices=None, item_ms=None, deadline_s=None, quota0=4096,
+                 quota_min=64):
         self.graphs = dict(graphs)
         self.slice_cycles = int(slice_ms * 1e-3 * clock_ghz * 1e9)
         # with item_ms, a single work item (edge task) that needs longer than
@@ -64,6 +86,8 @@ class Server:
         self.stream = stream
         self.max_slices = max_slices
         self.deadline_s = deadline_s      # wall-clock limit per request (from arrival)
+        self.quota0 = quota0              # first task window of a job (tasks per slice)
+        self.quota_min = quota_min
         self._plans = {}
         self._pending = collections.deque()
         self._active = []
@@ -119,6 +143,7 @@ class Server:
                 break
             self._pending.popleft()
             r.next_task, r.end_task = 0, self._nnz[r.graph]
+            r.quota = self.quota0
             self._active.append(r)
 
     def _loop(self):
@@ -132,11 +157,14 @@ class Server:
                 batch = list(self._active)
             if not batch:
                 continue
+            rot = self.slices % len(batch)              # every job at the front in turn
+            batch = batch[rot:] + batch[:rot]
+            window = [min(r.end_task, r.next_task + r.quota) for r in batch]
             opts = N.make_opts(budget_cycles=self.slice_cycles, task_cycles=self.item_cycles)
             try:
                 st, out, nxt = N.gp_count_batch_ranges(
                     [self.graphs[r.graph] for r in batch], [r.sched for r in batch],
-                    [0] * len(batch), [r.next_task for r in batch], [r.end_task for r in batch],
+                    [0] * len(batch), [r.next_task for r in batch], window,
                     opts, stream=self.stream)
             except Exception as e:
                 now = time.perf_counter()
@@ -150,7 +178,7 @@ class Server:
             now = time.perf_counter()
             with self._cv:
                 still = []
-                for r, c, t in zip(batch, out, nxt):
+                for r, c, t, w in zip(batch, out, nxt, window):
                     r.slices += 1
                     if int(t) < 0:                       # a work item outlived item_cycles
                         r.error = TimeoutError(f"request {r.rid}: a work item exceeded the item limit")
@@ -158,6 +186,7 @@ class Server:
                         r.done.set()
                         continue
                     r.acc += int(c)
+                    r.quota = next_quota(r.quota, int(t) - r.next_task, int(t) >= w, self.quota_min)
                     r.next_task = int(t)
                     if r.next_task >= r.end_task:
                         r.count, r.finish = r.acc, now
@@ -172,7 +201,8 @@ class Server:
                         r.done.set()
                     else:
                         still.append(r)
-                self._active = still
+                order = {id(r): i for i, r in enumerate(self._active)}
+                self._active = sorted(still, key=lambda r: order[id(r)])
 
 
 def poisson_arrivals(rate, count, seed):

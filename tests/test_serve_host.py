@@ -179,3 +179,58 @@ def test_failing_launch_answers_the_batch(fake):
     finally:
         srv.close()
     assert all(isinstance(r.error, RuntimeError) for r in reqs)
+
+
+class FakeCursor(FakeNative):
+    """Models the launch's task order: tasks of the jobs in the order given,
+    each costing `cost[k]` units, until the slice budget of `budget` units is
+    spent (the task that crosses it still completes)."""
+
+    def __init__(self, budget, cost):
+        super().__init__()
+        self.budget = budget
+        self.cost = cost
+
+    def gp_count_batch_ranges(self, graphs, scheds, idx, begin, end, opts, stream=None):
+        self.launches += 1
+        left = self.budget
+        out, nxt = [], []
+        for s, b, e in zip(scheds, begin, end):
+            t = b
+            while t < e and left > 0:
+                left -= self.cost[s.k]
+                t += 1
+            out.append((t - b) * s.k)
+            nxt.append(t)
+        return 0, np.array(out, np.uint64), np.array(nxt, np.int64)
+
+
+def test_quota_rule():
+    assert serve.next_quota(100, 100, True, 8) == 200           # finished: double
+    assert serve.next_quota(100, 40, False, 8) == 20            # cut: half of what it did
+    assert serve.next_quota(100, 3, False, 8) == 8              # never below the minimum
+    assert serve.next_quota(100, 0, False, 8) == 100            # no progress: unchanged
+
+
+def test_heavy_jobs_do_not_starve_the_rest(fake, monkeypatch):
+    # three 5-vertex jobs whose tasks cost 1000 units each over huge task
+    # ranges, submitted first, then light 3-vertex jobs (1 unit per task,
+    # 300 tasks); 20,000 units per slice
+    f = FakeCursor(budget=20000, cost={5: 1000, 3: 1})
+    monkeypatch.setattr(serve, "N", f)
+    srv = serve.Server({"big": FakeGraph(10 ** 7), "small": FakeGraph(300)}, slice_ms=1.0,
+                       quota0=4096, max_slices=100)
+    try:
+        heavy = [srv.submit("big", adj_k(5)) for _ in range(3)]
+        time.sleep(0.05)
+        light = [srv.submit("small", adj_k(3)) for _ in range(4)]
+        wait_all(light)
+        assert all(r.count == 900 and r.error is None for r in light)
+        # the light jobs finished within a few slices of their admission
+        assert max(r.slices for r in light) <= 3
+    finally:
+        srv.close()
+    wait_all(heavy)
+    assert all(isinstance(r.error, TimeoutError) for r in heavy)    # max_slices
+    # the heavy jobs' windows shrank below their first quota
+    assert all(r.quota < 4096 for r in heavy)
