@@ -321,3 +321,26 @@ def test_rmat20_sampled_roots(N, pname):
         st, c = N.gp_count(g, s, 0, o)
         expect = oracle.count_restricted(adj, order, res, ref, root_begin=r, root_end=r + 1)
         assert c == expect, (pname, r, int(deg[r]))
+
+
+@pytest.mark.parametrize("pname,roots", [("k6e", None), ("c6chord", [(9700, 10000), (2000, 2050)]),
+                                         ("grid3x2", [(9700, 10000), (2000, 2050)])])
+def test_chung_lu_six_vertex_patterns(N, pname, roots):
+    """The Chung-Lu workload's 6-vertex patterns on the same generator at
+    10,000 vertices (exponent 2.1, mean degree 17.5): the whole K6-e count,
+    and the counts of two root ranges (lowest-degree roots, and roots of
+    degree about 16) for the 6-cycle with a chord and the 3x2 grid, against
+    the oracle's restricted enumeration with the same plan."""
+    g, ref = graph_pair(N, "cl10000")
+    adj = named_pattern(pname)
+    # the plan ranked first under the library's default graph statistics
+    # (fixed, so that the oracle's share of the test stays within a minute)
+    s = N.gp_schedule(N.gp_pattern_create(adj), None)
+    order, res, _ = s.get(0)
+    if roots is None:
+        assert N.gp_count(g, s) == (N.GP_OK, oracle.count_restricted(adj, order, res, ref))
+        return
+    for lo, hi in roots:
+        o = N.make_opts(task_begin=int(ref.row_ptr[lo]), task_end=int(ref.row_ptr[hi]))
+        expect = oracle.count_restricted(adj, order, res, ref, root_begin=lo, root_end=hi)
+        assert N.gp_count(g, s, 0, o) == (N.GP_OK, expect), (pname, lo, hi)
