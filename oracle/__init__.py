@@ -45,26 +45,29 @@ def build(force=False):
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
-        P = ctypes.c_void_p
-        i32, i64 = ctypes.c_int32, ctypes.c_int64
-        lib.oracle_build_csr.argtypes = [i32, i64, P, P, P, P, P]
-        lib.oracle_aut_count.argtypes = [i32, P, P]
-        lib.oracle_count_maps.argtypes = [i32, P, i32, P, P, i32, i32, i32, i32, P, P]
-        lib.oracle_count.argtypes = [i32, P, i32, P, P, i32, P]
-        lib.oracle_count_restricted.argtypes = [i32, P, P, i32, P, i32, P, P, i32, i32, i32, P, P]
-        lib.oracle_triangles.argtypes = [i32, P, P, i32, P]
-        lib.oracle_list_restricted.argtypes = [i32, P, P, i32, P, i32, P, P, i32, i32, P, i64, P]
-        lib.oracle_list_restricted.restype = ctypes.c_int
-        lib.oracle_aut_count_labeled.argtypes = [i32, P, P, P]
-        lib.oracle_aut_count_labeled.restype = ctypes.c_int
-        lib.oracle_count_labeled.argtypes = [i32, P, P, i32, P, P, P, i32, P]
-        lib.oracle_count_labeled.restype = ctypes.c_int
-        for f in (lib.oracle_build_csr, lib.oracle_aut_count, lib.oracle_count_maps,
-                  lib.oracle_count, lib.oracle_count_restricted, lib.oracle_triangles):
-            f.restype = ctypes.c_int
-        _lib = lib
+        _lib = configure(ctypes.CDLL(build()))
     return _lib
+
+
+def configure(lib):
+    """Declare the C signatures on a loaded copy of ``oracle.c``'s library."""
+    P = ctypes.c_void_p
+    i32, i64 = ctypes.c_int32, ctypes.c_int64
+    lib.oracle_build_csr.argtypes = [i32, i64, P, P, P, P, P]
+    lib.oracle_aut_count.argtypes = [i32, P, P]
+    lib.oracle_count_maps.argtypes = [i32, P, i32, P, P, i32, i32, i32, i32, P, P]
+    lib.oracle_count_restricted.argtypes = [i32, P, P, i32, P, i32, P, P, i32, i32, i32, P, P]
+    lib.oracle_triangles.argtypes = [i32, P, P, i32, P]
+    lib.oracle_list_restricted.argtypes = [i32, P, P, i32, P, i32, P, P, i32, i32, P, i64, P]
+    lib.oracle_list_restricted.restype = ctypes.c_int
+    lib.oracle_aut_count_labeled.argtypes = [i32, P, P, P]
+    lib.oracle_aut_count_labeled.restype = ctypes.c_int
+    lib.oracle_count_labeled.argtypes = [i32, P, P, i32, P, P, P, i32, P]
+    lib.oracle_count_labeled.restype = ctypes.c_int
+    for f in (lib.oracle_build_csr, lib.oracle_aut_count, lib.oracle_count_maps,
+              lib.oracle_count_restricted, lib.oracle_triangles):
+        f.restype = ctypes.c_int
+    return lib
 
 
 def _p(a):

@@ -254,22 +254,6 @@ int oracle_count_maps(int32_t k, const uint8_t* adj,
     return 0;
 }
 
-int oracle_count(int32_t k, const uint8_t* adj,
-                 int32_t n, const int64_t* row_ptr, const int32_t* col,
-                 int32_t nthreads, uint64_t* out) {
-    uint64_t hi, lo, aut;
-    int rc = oracle_aut_count(k, adj, &aut);
-    if (rc) return rc;
-    rc = oracle_count_maps(k, adj, n, row_ptr, col, 0, n, 1, nthreads, &hi, &lo);
-    if (rc) return rc;
-    u128 maps = ((u128)hi << 64) | lo;
-    if (maps % aut) return -3;
-    u128 q = maps / aut;
-    if (q >> 64) return -4;
-    *out = (uint64_t)q;
-    return 0;
-}
-
 int oracle_count_restricted(int32_t k, const uint8_t* adj, const int32_t* order,
                             int32_t nres, const int32_t* res,
                             int32_t n, const int64_t* row_ptr, const int32_t* col,

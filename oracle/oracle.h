@@ -48,13 +48,6 @@ int oracle_count_maps(int32_t k, const uint8_t* adj,
                       int32_t root_begin, int32_t root_end, int32_t root_stride,
                       int32_t nthreads, uint64_t* hi, uint64_t* lo);
 
-/* count(P, G) = maps / |Aut(P)| over all roots. Returns -3 when the maps are
- * not a multiple of |Aut(P)| (impossible for a correct enumeration) and -4
- * when the count does not fit in 64 bits. */
-int oracle_count(int32_t k, const uint8_t* adj,
-                 int32_t n, const int64_t* row_ptr, const int32_t* col,
-                 int32_t nthreads, uint64_t* out);
-
 /* Maps enumerated in the given matching order (Section II-B) that also obey
  * every restriction id(res[2i]) > id(res[2i+1]) (Section II-B), with the
  * image of the first searched vertex in [root_begin, root_end). Vertices are
@@ -82,8 +75,11 @@ int oracle_list_restricted(int32_t k, const uint8_t* adj, const int32_t* order,
  * extends to labelled graphs): a map must also send every pattern vertex to
  * a graph vertex of the same label. plabels has k entries, glabels n.
  * oracle_aut_count_labeled counts the automorphisms that preserve labels;
- * oracle_count_labeled returns maps / labelled |Aut| (-3 / -4 as for
- * oracle_count). */
+ * oracle_count_labeled returns maps / labelled |Aut|; it returns -3 when the
+ * maps are not a multiple of it (impossible for a correct enumeration) and
+ * -4 when the count does not fit in 64 bits. (The unlabelled count(P, G) =
+ * maps / |Aut(P)| is taken in Python from oracle_count_maps and
+ * oracle_aut_count, where it may exceed 64 bits.) */
 int oracle_aut_count_labeled(int32_t k, const uint8_t* adj, const int32_t* plabels, uint64_t* out);
 int oracle_count_labeled(int32_t k, const uint8_t* adj, const int32_t* plabels,
                          int32_t n, const int64_t* row_ptr, const int32_t* col,
