@@ -64,8 +64,12 @@ def configure(lib):
     lib.oracle_aut_count_labeled.restype = ctypes.c_int
     lib.oracle_count_labeled.argtypes = [i32, P, P, i32, P, P, P, i32, P]
     lib.oracle_count_labeled.restype = ctypes.c_int
+    lib.oracle_build_dcsr.argtypes = [i32, i64, P, P, P, P, P, P, P]
+    lib.oracle_aut_count_directed.argtypes = [i32, P, P]
+    lib.oracle_count_directed.argtypes = [i32, P, P, i32, P, i32, P, P, P, P, i32, i32, i32, P, P]
     for f in (lib.oracle_build_csr, lib.oracle_aut_count, lib.oracle_count_maps,
-              lib.oracle_count_restricted, lib.oracle_triangles):
+              lib.oracle_count_restricted, lib.oracle_triangles, lib.oracle_build_dcsr,
+              lib.oracle_aut_count_directed, lib.oracle_count_directed):
         f.restype = ctypes.c_int
     return lib
 
@@ -229,3 +233,86 @@ def triangles(g, threads=None):
     if rc:
         raise ValueError(f"oracle_triangles failed ({rc})")
     return int(out[0])
+
+
+# ---------------------------------------------------------------- directed
+
+class DCsr:
+    """Directed simple graph: sorted out-lists and in-lists."""
+
+    def __init__(self, n, out_ptr, out_col, in_ptr, in_col):
+        self.n = n
+        self.out_ptr, self.out_col = out_ptr, out_col
+        self.in_ptr, self.in_col = in_ptr, in_col
+
+    @property
+    def narcs(self):
+        return int(self.out_ptr[-1])
+
+
+def build_dcsr(n, src, dst):
+    """Arcs src[i] -> dst[i]: loops dropped, repeated arcs kept once."""
+    src = np.ascontiguousarray(src, dtype=np.int32)
+    dst = np.ascontiguousarray(dst, dtype=np.int32)
+    m = len(src)
+    out_ptr = np.zeros(n + 1, dtype=np.int64)
+    in_ptr = np.zeros(n + 1, dtype=np.int64)
+    out_col = np.zeros(max(1, m), dtype=np.int32)
+    in_col = np.zeros(max(1, m), dtype=np.int32)
+    narcs = np.zeros(1, dtype=np.int64)
+    rc = _load().oracle_build_dcsr(n, m, _p(src), _p(dst), _p(out_ptr), _p(out_col), _p(in_ptr), _p(in_col),
+                                   _p(narcs))
+    if rc:
+        raise ValueError(f"oracle_build_dcsr failed ({rc})")
+    a = int(narcs[0])
+    return DCsr(n, out_ptr, out_col[:a].copy(), in_ptr, in_col[:a].copy())
+
+
+def _dadj(adj):
+    adj = np.ascontiguousarray(adj, dtype=np.uint8)
+    if adj.ndim != 2 or adj.shape[0] != adj.shape[1]:
+        raise ValueError("adjacency must be k x k")
+    return adj
+
+
+def aut_count_directed(adj):
+    """Arc-preserving permutations of a directed pattern."""
+    adj = _dadj(adj)
+    out = np.zeros(1, dtype=np.uint64)
+    rc = _load().oracle_aut_count_directed(adj.shape[0], _p(adj), _p(out))
+    if rc:
+        raise ValueError(f"oracle_aut_count_directed failed ({rc})")
+    return int(out[0])
+
+
+def count_maps_directed(adj, dg, order=None, restrictions=(), root_begin=0, root_end=None, threads=None):
+    """Injective arc-preserving maps (obeying the restrictions, with the
+    first searched vertex's image in [root_begin, root_end))."""
+    adj = _dadj(adj)
+    k = adj.shape[0]
+    o = None if order is None else np.ascontiguousarray(order, dtype=np.int32)
+    res = np.ascontiguousarray(np.array(restrictions, dtype=np.int32).reshape(-1, 2))
+    nres = res.shape[0]
+    if nres == 0:
+        res = np.zeros((1, 2), dtype=np.int32)
+    hi = np.zeros(1, dtype=np.uint64)
+    lo = np.zeros(1, dtype=np.uint64)
+    dummy = np.zeros(1, dtype=np.int32)
+    rc = _load().oracle_count_directed(k, _p(adj), None if o is None else _p(o), nres, _p(res), dg.n,
+                                       _p(dg.out_ptr), _p(dg.out_col if dg.narcs else dummy),
+                                       _p(dg.in_ptr), _p(dg.in_col if dg.narcs else dummy),
+                                       root_begin, dg.n if root_end is None else root_end,
+                                       threads or default_threads(), _p(hi), _p(lo))
+    if rc:
+        raise ValueError(f"oracle_count_directed failed ({rc})")
+    return (int(hi[0]) << 64) | int(lo[0])
+
+
+def count_directed(adj, dg, threads=None):
+    """count(P, G) = arc-preserving injective maps / |Aut(P)|."""
+    maps = count_maps_directed(adj, dg, threads=threads)
+    aut = aut_count_directed(adj)
+    if maps % aut:
+        raise AssertionError("map count is not a multiple of |Aut(P)|")
+    return maps // aut
+

@@ -433,3 +433,209 @@ int oracle_triangles(int32_t n, const int64_t* row_ptr, const int32_t* col,
     free(ws); free(th);
     return 0;
 }
+
+/* ------------------------------------------------------ directed patterns */
+/* A directed pattern has arcs a -> b (adj[a * k + b] = 1; not necessarily
+ * symmetric). An embedding is an injective map f sending every pattern arc
+ * a -> b to a graph arc f(a) -> f(b) (non-induced); the count is maps /
+ * |Aut(P)|, Aut(P) being the arc-preserving permutations. The graph keeps
+ * both the out-arcs and the in-arcs of every vertex as sorted lists. */
+
+static int build_sorted_lists(int32_t n, int64_t m, const uint64_t* keys, int64_t* ptr, int32_t* col) {
+    for (int32_t v = 0; v <= n; ++v) ptr[v] = 0;
+    for (int64_t i = 0; i < m; ++i) ptr[(keys[i] >> 32) + 1]++;
+    for (int32_t v = 0; v < n; ++v) ptr[v + 1] += ptr[v];
+    for (int64_t i = 0; i < m; ++i) col[i] = (int32_t)(keys[i] & 0xffffffffu);
+    return 0;
+}
+
+int oracle_build_dcsr(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                      int64_t* out_ptr, int32_t* out_col, int64_t* in_ptr, int32_t* in_col,
+                      int64_t* narcs) {
+    if (n < 0 || m < 0 || (m > 0 && (!src || !dst)) || !out_ptr || !in_ptr || !narcs) return -1;
+    uint64_t* fwd = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(m + 1));
+    uint64_t* rev = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(m + 1));
+    if (!fwd || !rev) { free(fwd); free(rev); return -2; }
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < m; ++i) {
+        int32_t u = src[i], v = dst[i];
+        if (u < 0 || u >= n || v < 0 || v >= n) { free(fwd); free(rev); return -1; }
+        if (u != v)                                             /* a loop is not an arc */
+            fwd[cnt++] = ((uint64_t)(uint32_t)u << 32) | (uint32_t)v;
+    }
+    qsort(fwd, (size_t)cnt, sizeof(uint64_t), cmp_u64);
+    int64_t uniq = 0;
+    for (int64_t i = 0; i < cnt; ++i)                            /* one copy of each arc */
+        if (uniq == 0 || fwd[i] != fwd[uniq - 1]) fwd[uniq++] = fwd[i];
+    for (int64_t i = 0; i < uniq; ++i)                           /* the same arcs by head */
+        rev[i] = ((fwd[i] & 0xffffffffu) << 32) | (fwd[i] >> 32);
+    qsort(rev, (size_t)uniq, sizeof(uint64_t), cmp_u64);
+    build_sorted_lists(n, uniq, fwd, out_ptr, out_col);
+    build_sorted_lists(n, uniq, rev, in_ptr, in_col);
+    *narcs = uniq;
+    free(fwd); free(rev);
+    return 0;
+}
+
+int oracle_aut_count_directed(int32_t k, const uint8_t* adj, uint64_t* out) {
+    if (k < 1 || k > 10 || !adj || !out) return -1;
+    int p[10];
+    for (int i = 0; i < k; ++i) p[i] = i;
+    uint64_t c = 0;
+    do {
+        int keeps_arcs = 1;
+        for (int a = 0; a < k; ++a)
+            for (int b = 0; b < k; ++b)
+                if (adj[a * k + b] && !adj[p[a] * k + p[b]]) keeps_arcs = 0;
+        c += (uint64_t)keeps_arcs;
+    } while (next_perm(p, k));
+    *out = c;
+    return 0;
+}
+
+typedef struct {
+    int k;
+    int order[8];
+    int anchor[8];          /* earlier depth joined to depth d by an arc            */
+    int from_out[8];        /* 1: candidates are the out-arcs of the anchor's image */
+    int nchk[8];
+    int chk_depth[8][16];   /* further arcs to verify at depth d ...                */
+    int chk_fwd[8][16];     /* ... 1: image(j) -> v, 0: v -> image(j)              */
+    int nres[8];
+    int res_other[8][32];
+    int res_gt[8][32];
+    int32_t n;
+    const int64_t *out_ptr, *in_ptr;
+    const int32_t *out_col, *in_col;
+    int32_t root_begin, root_end;
+    atomic_long cursor;
+} dwalk_t;
+
+static int arc_present(const dwalk_t* w, int32_t u, int32_t v) {   /* u -> v ? */
+    int64_t lo = w->out_ptr[u], hi = w->out_ptr[u + 1];
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (w->out_col[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo < w->out_ptr[u + 1] && w->out_col[lo] == v;
+}
+
+static u128 dwalk(const dwalk_t* w, int d, int32_t* img) {
+    if (d == w->k) return 1;
+    const int32_t a = img[w->anchor[d]];
+    const int64_t* ptr = w->from_out[d] ? w->out_ptr : w->in_ptr;
+    const int32_t* col = w->from_out[d] ? w->out_col : w->in_col;
+    u128 total = 0;
+    for (int64_t e = ptr[a]; e < ptr[a + 1]; ++e) {
+        const int32_t v = col[e];
+        int good = 1;
+        for (int j = 0; j < d; ++j) good &= (img[j] != v);                      /* injective */
+        for (int c = 0; c < w->nchk[d] && good; ++c) {
+            const int32_t o = img[w->chk_depth[d][c]];
+            good = w->chk_fwd[d][c] ? arc_present(w, o, v) : arc_present(w, v, o);
+        }
+        for (int r = 0; r < w->nres[d] && good; ++r) {
+            const int32_t o = img[w->res_other[d][r]];
+            good = w->res_gt[d][r] ? (v > o) : (v < o);
+        }
+        if (!good) continue;
+        img[d] = v;
+        total += dwalk(w, d + 1, img);
+    }
+    return total;
+}
+
+typedef struct { dwalk_t* w; u128 sum; } dworker_t;
+
+static void* dworker_main(void* arg) {
+    dworker_t* me = (dworker_t*)arg;
+    int32_t img[8];
+    for (;;) {
+        long r = atomic_fetch_add(&me->w->cursor, 1) + me->w->root_begin;
+        if (r >= me->w->root_end) break;
+        img[0] = (int32_t)r;
+        me->sum += dwalk(me->w, 1, img);
+    }
+    return NULL;
+}
+
+int oracle_count_directed(int32_t k, const uint8_t* adj, const int32_t* order,
+                          int32_t nres, const int32_t* res,
+                          int32_t n, const int64_t* out_ptr, const int32_t* out_col,
+                          const int64_t* in_ptr, const int32_t* in_col,
+                          int32_t root_begin, int32_t root_end, int32_t nthreads,
+                          uint64_t* hi, uint64_t* lo) {
+    if (k < 2 || k > 8 || !adj || !hi || !lo || n < 0 || !out_ptr || !in_ptr || (nres > 0 && !res))
+        return -1;
+    dwalk_t* w = (dwalk_t*)calloc(1, sizeof(dwalk_t));
+    if (!w) return -2;
+    w->k = k; w->n = n;
+    w->out_ptr = out_ptr; w->out_col = out_col; w->in_ptr = in_ptr; w->in_col = in_col;
+    int pos[8], seen[8] = {0};
+    if (order) {
+        for (int d = 0; d < k; ++d) {
+            if (order[d] < 0 || order[d] >= k || seen[order[d]]) { free(w); return -1; }
+            seen[order[d]] = 1;
+            w->order[d] = order[d];
+        }
+    } else {                                  /* breadth-first over arcs of either direction */
+        int head = 0, tail = 0;
+        w->order[tail++] = 0; seen[0] = 1;
+        while (head < tail) {
+            const int x = w->order[head++];
+            for (int y = 0; y < k; ++y)
+                if ((adj[x * k + y] || adj[y * k + x]) && !seen[y]) { seen[y] = 1; w->order[tail++] = y; }
+        }
+        if (tail != k) { free(w); return -1; }
+    }
+    for (int d = 0; d < k; ++d) pos[w->order[d]] = d;
+    for (int a = 0; a < k; ++a) if (adj[a * k + a]) { free(w); return -1; }
+    for (int d = 1; d < k; ++d) {
+        const int x = w->order[d];
+        w->anchor[d] = -1;
+        for (int j = 0; j < d; ++j) {
+            const int y = w->order[j];
+            const int to_x = adj[y * k + x], from_x = adj[x * k + y];
+            if (!to_x && !from_x) continue;
+            if (w->anchor[d] < 0) {
+                w->anchor[d] = j;
+                w->from_out[d] = to_x;        /* y -> x: x among the out-arcs of img(y) */
+                if (to_x && from_x) {         /* the arc back still needs a check */
+                    w->chk_depth[d][w->nchk[d]] = j; w->chk_fwd[d][w->nchk[d]++] = 0;
+                }
+                continue;
+            }
+            if (to_x) { w->chk_depth[d][w->nchk[d]] = j; w->chk_fwd[d][w->nchk[d]++] = 1; }
+            if (from_x) { w->chk_depth[d][w->nchk[d]] = j; w->chk_fwd[d][w->nchk[d]++] = 0; }
+        }
+        if (w->anchor[d] < 0) { free(w); return -1; }   /* every prefix must be weakly connected */
+    }
+    for (int r = 0; r < nres; ++r) {
+        const int a = res[2 * r], b = res[2 * r + 1];   /* id(a) > id(b) */
+        if (a < 0 || a >= k || b < 0 || b >= k || a == b) { free(w); return -1; }
+        const int da = pos[a], db = pos[b], later = da > db ? da : db;
+        if (w->nres[later] >= 32) { free(w); return -1; }
+        w->res_other[later][w->nres[later]] = da > db ? db : da;
+        w->res_gt[later][w->nres[later]] = (later == da);
+        w->nres[later]++;
+    }
+    if (root_begin < 0) root_begin = 0;
+    if (root_end > n) root_end = n;
+    if (root_end < root_begin) root_end = root_begin;
+    w->root_begin = root_begin; w->root_end = root_end;
+    atomic_store(&w->cursor, 0);
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 512) nthreads = 512;
+    dworker_t* ws = (dworker_t*)calloc((size_t)nthreads, sizeof(dworker_t));
+    pthread_t* th = (pthread_t*)calloc((size_t)nthreads, sizeof(pthread_t));
+    if (!ws || !th) { free(ws); free(th); free(w); return -2; }
+    for (int t = 0; t < nthreads; ++t) ws[t].w = w;
+    for (int t = 1; t < nthreads; ++t)
+        if (pthread_create(&th[t], NULL, dworker_main, &ws[t]) != 0) ws[t].w = NULL;
+    dworker_main(&ws[0]);
+    u128 s = ws[0].sum;
+    for (int t = 1; t < nthreads; ++t) if (ws[t].w) { pthread_join(th[t], NULL); s += ws[t].sum; }
+    split128(s, hi, lo);
+    free(ws); free(th); free(w);
+    return 0;
+}

@@ -91,6 +91,30 @@ int oracle_count_labeled(int32_t k, const uint8_t* adj, const int32_t* plabels,
 int oracle_triangles(int32_t n, const int64_t* row_ptr, const int32_t* col,
                      int32_t nthreads, uint64_t* out);
 
+/* Directed patterns and graphs (the paper mentions directed patterns without
+ * defining them; reading: an embedding is an injective map sending every
+ * pattern arc a -> b, adj[a * k + b] = 1, to a graph arc, non-induced, and
+ * the count is maps / |Aut(P)| over arc-preserving permutations).
+ * oracle_build_dcsr: m arcs src[i] -> dst[i] (loops dropped, repeats merged)
+ * into out-lists (out_ptr n + 1, out_col) and in-lists (in_ptr, in_col),
+ * each sorted; *narcs receives the number of distinct arcs.
+ * oracle_aut_count_directed: |Aut(P)| over arc-preserving permutations.
+ * oracle_count_directed: maps whose first searched vertex (order[0]; order
+ * NULL = breadth-first over arcs of either direction from vertex 0) has its
+ * image in [root_begin, root_end), obeying the restrictions id(res[2i]) >
+ * id(res[2i+1]); every prefix of the order must be weakly connected. The
+ * 128-bit total is returned in (*hi, *lo). */
+int oracle_build_dcsr(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                      int64_t* out_ptr, int32_t* out_col, int64_t* in_ptr, int32_t* in_col,
+                      int64_t* narcs);
+int oracle_aut_count_directed(int32_t k, const uint8_t* adj, uint64_t* out);
+int oracle_count_directed(int32_t k, const uint8_t* adj, const int32_t* order,
+                          int32_t nres, const int32_t* res,
+                          int32_t n, const int64_t* out_ptr, const int32_t* out_col,
+                          const int64_t* in_ptr, const int32_t* in_col,
+                          int32_t root_begin, int32_t root_end, int32_t nthreads,
+                          uint64_t* hi, uint64_t* lo);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,6 +35,10 @@ MUTANTS = [
      "    u128 q = maps / (aut > 1 ? aut / 2 : aut);"),
     ("triangles_counted_twice", "                    if (c <= b) continue;\n", ""),
     ("ignores_graph_labels", "if (ok && w->glab && w->glab[v] != w->plab[d]) ok = 0;", ";"),
+    ("directed_ignores_arc_direction", "good = w->chk_fwd[d][c] ? arc_present(w, o, v) : arc_present(w, v, o);",
+     "good = arc_present(w, o, v) || arc_present(w, v, o);"),
+    ("directed_keeps_repeated_arcs", "if (uniq == 0 || fwd[i] != fwd[uniq - 1]) fwd[uniq++] = fwd[i];",
+     "fwd[uniq++] = fwd[i];"),
     ("listing_not_injective", "        for (int j = 0; j < d && ok; ++j) if (img[j] == v) ok = 0;\n        for (int c = 0; c < w->nchk[d] && ok; ++c)\n            if (!has_edge(w, img[w->chk[d][c]], v)) ok = 0;\n        for (int r = 0; r < w->nres[d] && ok; ++r) {\n            int32_t o",
      "        for (int c = 0; c < w->nchk[d] && ok; ++c)\n            if (!has_edge(w, img[w->chk[d][c]], v)) ok = 0;\n        for (int r = 0; r < w->nres[d] && ok; ++r) {\n            int32_t o"),
 ]
@@ -97,6 +101,16 @@ def battery():
         check("labels", oracle.count_labeled(named_pattern("c4"), [0, 1, 0, 1], bipartite(a, b), gl)
               == math.comb(a, 2) * math.comb(b, 2)
               and oracle.count_labeled(named_pattern("c4"), [0, 0, 1, 1], bipartite(a, b), gl) == 0)
+        # directed: hand-worked lists, a transitive tournament, a complete digraph
+        dg = oracle.build_dcsr(3, np.array([0, 1, 1, 0], np.int32), np.array([1, 0, 2, 1], np.int32))
+        check("dcsr", list(dg.out_ptr) == [0, 1, 3, 3] and list(dg.out_col) == [1, 0, 2])
+        cyc3 = np.zeros((3, 3), np.uint8)
+        cyc3[0, 1] = cyc3[1, 2] = cyc3[2, 0] = 1
+        ff = np.zeros((3, 3), np.uint8)
+        ff[0, 1] = ff[0, 2] = ff[1, 2] = 1
+        t6 = [(i, j) for i in range(6) for j in range(i + 1, 6)]
+        T = oracle.build_dcsr(6, np.array([a for a, _ in t6], np.int32), np.array([b for _, b in t6], np.int32))
+        check("tournament", oracle.count_directed(cyc3, T) == 0 and oracle.count_directed(ff, T) == 20)
     except Exception as e:              # a mutant may also break an internal consistency check
         failed.append(f"raised {type(e).__name__}")
     return failed
