@@ -11,9 +11,9 @@ paper's performance model.
 
 Readings of the paper used here (each also listed in the design notes):
 
-* Algorithm 1 tests ``vertex = perm[perm[vertex]]`` to find a 2-cycle; a
-  fixed point also passes that test, so ``perm[vertex] != vertex`` is required
-  too, and the pair added is ``(vertex, perm[vertex])``.
+* Algorithm 1 finds a 2-cycle as a vertex that is the image of its own
+  image; a fixed point also meets that test, so the vertex must also differ
+  from its image, and the pair added is ``(vertex, perm[vertex])``.
 * ``generate`` depends on its arguments only through ``res_set``: the group
   it receives is exactly the automorphisms not yet eliminated by
   ``res_set``, because ``no_conflict`` is monotone (a permutation that closes a
