@@ -146,9 +146,20 @@ def phase2_ok(adj, sched, kk):
     return all(not adj[a][b] for a, b in combinations(tail, 2))
 
 
+def underlying(adj):
+    """The undirected pattern under a directed one (an edge wherever an arc
+    runs either way); an undirected pattern is its own."""
+    k = len(adj)
+    return [[1 if (adj[a][b] or adj[b][a]) else 0 for b in range(k)] for a in range(k)]
+
+
 def efficient_schedules(adj):
     """(schedules, k') : the 2-phase filter with phase 2 relaxed to the
-    largest k' that keeps a schedule."""
+    largest k' that keeps a schedule. For a directed pattern both phases
+    look at its underlying undirected pattern (a vertex joined to an earlier
+    one by an arc of either direction has its candidates in that vertex's
+    out- or in-list)."""
+    adj = underlying(adj)
     k = len(adj)
     p1 = [s for s in permutations(range(k)) if phase1_ok(adj, s)]
     for kk in range(max_independent_set_size(adj), 0, -1):

@@ -159,3 +159,20 @@ def test_root_ranges_partition_the_maps():
     total = oracle.count_maps_directed(MIXED4, g)
     parts = sum(oracle.count_maps_directed(MIXED4, g, root_begin=b, root_end=b + 7) for b in range(0, n, 7))
     assert parts == total
+
+
+@pytest.mark.parametrize("p", [CYCLE3, PATH3, FEED_FORWARD, CYCLE4, BIFAN, MIXED4],
+                         ids=["cycle3", "path3", "feed_forward", "cycle4", "bifan", "mixed4"])
+def test_directed_schedules_follow_the_underlying_pattern(p):
+    # every efficient schedule keeps each prefix weakly connected, so the
+    # directed oracle accepts it as a matching order, and every order gives
+    # the same count
+    al = p.tolist()
+    scheds, kk = pr.efficient_schedules(al)
+    und = pr.underlying(al)
+    assert (scheds, kk) == pr.efficient_schedules(und)
+    n, s, d = random_digraph(25, 150, 9)
+    g = oracle.build_dcsr(n, s, d)
+    base = oracle.count_maps_directed(p, g)
+    for sc in scheds[:6]:
+        assert oracle.count_maps_directed(p, g, order=sc) == base
