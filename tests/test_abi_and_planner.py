@@ -111,3 +111,57 @@ def test_labeled_planner_matches_oracle(N, name, labels):
     p = N.gp_pattern_create_labeled(adj, labels)
     assert p.aut_count() == len(pr.automorphisms(adj.tolist(), labels)) == oracle.aut_count_labeled(adj, labels)
     assert set(p.restriction_sets()) == set(pr.restriction_sets(adj.tolist(), labels))
+
+
+def test_status_strings_cover_every_code(N):
+    lib = N.lib()
+    seen = set()
+    for code in (0, 1, -1, -2, -3, -4, -5, -6, -7, -8):
+        s = lib.gp_status_str(code).decode()
+        assert s and s not in seen, code
+        seen.add(s)
+    assert lib.gp_status_str(-99).decode()                 # unknown codes still get a string
+
+
+def test_host_calls_reject_bad_arguments(N):
+    import ctypes
+    lib = N.lib()
+    out = ctypes.c_void_p()
+    adj = np.ascontiguousarray(named_pattern("house"), dtype=np.uint8)
+    assert lib.gp_pattern_create(None, 5, ctypes.byref(out)) == N.GP_ERR_ARG
+    assert lib.gp_pattern_create(adj.ctypes.data_as(ctypes.c_void_p), 5, None) == N.GP_ERR_ARG
+    assert lib.gp_pattern_create_labeled(adj.ctypes.data_as(ctypes.c_void_p), None, 5,
+                                         ctypes.byref(out)) == N.GP_ERR_ARG
+    assert lib.gp_last_error().decode()                    # the failure left a message
+    p = N.gp_pattern_create(adj)
+    s = N.gp_schedule(p, None, top_k=2)
+    order = (ctypes.c_int32 * 7)()
+    assert lib.gp_schedule_get(s.h, 5, order, None, None, None) == N.GP_ERR_ARG   # idx out of range
+    assert lib.gp_schedule_get(s.h, -1, order, None, None, None) == N.GP_ERR_ARG
+    cnt = ctypes.c_int32()
+    assert lib.gp_schedule_size(s.h, ctypes.byref(cnt)) == N.GP_OK and cnt.value == 2
+    assert lib.gp_schedule(p.h, None, 0, None, ctypes.byref(out)) == N.GP_ERR_ARG   # top_k >= 1
+
+
+def test_iep_switch_on_plans_that_do_not_qualify(N):
+    import ctypes
+    lib = N.lib()
+    n_iep = ctypes.c_int32(-1)
+    tri = N.gp_schedule(N.gp_pattern_create(named_pattern("triangle")), None)
+    assert lib.gp_schedule_set_iep(tri.h, 1, ctypes.byref(n_iep)) == N.GP_OK and n_iep.value == 0
+    k4 = N.gp_schedule(N.gp_pattern_create(named_pattern("k4")), None)        # last two adjacent
+    assert lib.gp_schedule_set_iep(k4.h, 1, ctypes.byref(n_iep)) == N.GP_OK and n_iep.value == 0
+    house = N.gp_schedule(N.gp_pattern_create(named_pattern("house")), None, top_k=3)
+    assert lib.gp_schedule_set_iep(house.h, 1, ctypes.byref(n_iep)) == N.GP_OK and n_iep.value >= 1
+    assert lib.gp_schedule_set_iep(house.h, 0, ctypes.byref(n_iep)) == N.GP_OK
+
+
+def test_labeled_pattern_groups(N):
+    # equal labels give the plain group; alternating labels keep the
+    # rotations by two and the reflections that fix the label classes;
+    # distinct labels leave the identity
+    adj = named_pattern("c4")
+    p = N.gp_pattern_create_labeled(adj, [3, 3, 3, 3])
+    assert p.aut_count() == N.gp_pattern_create(adj).aut_count() == 8
+    assert N.gp_pattern_create_labeled(adj, [0, 1, 0, 1]).aut_count() == 4
+    assert N.gp_pattern_create_labeled(adj, [0, 1, 2, 3]).aut_count() == 1
