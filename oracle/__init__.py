@@ -321,3 +321,58 @@ def count_directed(adj, dg, threads=None):
         raise AssertionError("map count is not a multiple of |Aut(P)|")
     return maps // aut
 
+
+# ------------------------------------------------------ inclusion-exclusion
+
+def iep_total(adj, sched, restrictions, kk, g):
+    """Section IV-D on a small graph, in plain Python: enumerate the first
+    k - kk searched vertices (edges and the restrictions among them
+    checked), then, instead of looping over the last kk vertices (pairwise
+    non-adjacent, all their pattern neighbours among the first k - kk),
+    count the tuples of distinct vertices from their candidate sets with
+    the inclusion-exclusion expansion of ``planner_ref.iep_count``
+    (Algorithm 2 for every term). Candidate sets exclude the matched
+    vertices. Restrictions that involve a last-kk vertex are dropped, as the
+    paper drops them; the caller divides by the multiplicity."""
+    from .planner_ref import iep_count
+    adj = _adj(adj)
+    k = adj.shape[0]
+    outer, inner = list(sched[:k - kk]), list(sched[k - kk:])
+    for a in inner:
+        for b in inner:
+            if a != b and adj[a, b]:
+                raise ValueError("the last kk searched vertices must be pairwise non-adjacent")
+    nbr = [set(g.col[g.row_ptr[v]:g.row_ptr[v + 1]].tolist()) for v in range(g.n)]
+    ro = [(a, b) for a, b in restrictions if a in outer and b in outer]
+    pos = {v: i for i, v in enumerate(outer)}
+    img = {}
+    total = 0
+
+    def rec(d):
+        nonlocal total
+        if d == len(outer):
+            used = set(img.values())
+            sets = []
+            for u in inner:
+                cand = None
+                for w in range(k):
+                    if adj[u, w]:
+                        cand = set(nbr[img[w]]) if cand is None else cand & nbr[img[w]]
+                sets.append((cand if cand is not None else set(range(g.n))) - used)
+            total += iep_count(sets)
+            return
+        x = outer[d]
+        earlier = [w for w in outer[:d] if adj[x, w]]
+        cands = set(range(g.n)) if not earlier else set.intersection(*(nbr[img[w]] for w in earlier))
+        for v in sorted(cands):
+            if v in img.values():
+                continue
+            if any((a == x and pos[b] < d and not v > img[b]) or (b == x and pos[a] < d and not img[a] > v)
+                   for a, b in ro):
+                continue
+            img[x] = v
+            rec(d + 1)
+            del img[x]
+    rec(0)
+    return total
+

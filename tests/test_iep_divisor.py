@@ -1,8 +1,10 @@
-"""Host-side check of the inclusion-exclusion divisor (no GPU): the exact
-multiplicity of embeddings under the outer restrictions, counted over all
-k! relative orders, against the paper's no_conflict count. Where the two
-differ the exact one is right, shown by brute force on a small graph with
-the oracle's restricted enumerator."""
+"""Host-side checks of inclusion-exclusion counting (no GPU). The divisor:
+the exact multiplicity of embeddings under the outer restrictions, counted
+over all k! relative orders, against the paper's no_conflict count; where
+the two differ the exact one is right, shown on a small graph with the
+oracle's restricted enumerator. The expansion: for any number kk of last
+loops, the count by Algorithm 2's terms equals the enumeration with the
+outer restrictions only."""
 
 from itertools import permutations
 
@@ -50,3 +52,57 @@ def test_grid_configuration_where_paper_divisor_differs():
         if found:
             break
     assert found
+
+
+# ------------------------------------------------- Section IV-D, any k
+
+def three_ears():
+    # a triangle A, B, C with D on A-B, E on B-C, F on A-C: D, E, F are
+    # pairwise non-adjacent and all their neighbours lie in the triangle
+    import numpy as np
+    a = np.zeros((6, 6), np.uint8)
+    for x, y in [(0, 1), (1, 2), (0, 2), (3, 0), (3, 1), (4, 1), (4, 2), (5, 0), (5, 2)]:
+        a[x, y] = a[y, x] = 1
+    return a
+
+
+def star(leaves):
+    import numpy as np
+    a = np.zeros((leaves + 1, leaves + 1), np.uint8)
+    a[0, 1:] = a[1:, 0] = 1
+    return a
+
+
+import pytest  # noqa: E402
+
+
+@pytest.mark.parametrize("name,kk", [("house", 2), ("three_ears", 3), ("star4", 3), ("star5", 4)])
+def test_iep_expansion_counts_like_enumeration(name, kk):
+    """The inclusion-exclusion count over the last kk loops (Algorithm 2 for
+    every term) equals the enumeration with the outer restrictions only, and
+    that equals the count times the exact multiplicity when the
+    multiplicity is the same for every relative order."""
+    p = {"three_ears": three_ears, "star4": lambda: star(3), "star5": lambda: star(4)}.get(
+        name, lambda: named_pattern(name))()
+    adj = p.tolist()
+    k = len(adj)
+    n = 22
+    s, d = er_edges(n, 110, seed=kk)
+    g = oracle.build_csr(n, s, d)
+    truth = oracle.count(p, g)
+    scheds, kprime = pr.efficient_schedules(adj)
+    assert kprime >= kk
+    sets = pr.restriction_sets(adj)
+    checked = 0
+    for sc in scheds[:4]:
+        for rs in sets[:3]:
+            pos = {v: i for i, v in enumerate(sc)}
+            ro = [(a, b) for a, b in rs if max(pos[a], pos[b]) < k - kk]
+            total = oracle.iep_total(p, sc, rs, kk, g)
+            assert total == oracle.count_restricted(p, sc, ro, g)
+            m = {sum(1 for sg in pr.automorphisms(adj) if all(pi[sg[a]] > pi[sg[b]] for a, b in ro))
+                 for pi in permutations(range(k))}
+            if len(m) == 1:
+                assert total == truth * next(iter(m))
+            checked += 1
+    assert checked > 0
