@@ -263,11 +263,39 @@ def allreduce_counts(counts, device=None):
 
 # ------------------------------------------------------------------ GPU arm
 
+def _code_only(text):
+    """C/C++/CUDA source without comments and with whitespace runs collapsed:
+    what the compiler sees, so that editing a comment keeps a recorded
+    measurement valid."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c == '"' or c == "'":                       # literal: copy through its end
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def source_hash():
+    """Hash of the count kernel's code and of the planner that compiles its
+    plans, comments excluded."""
     h = hashlib.sha256()
     for f in ("count.cu", "plan.h", "planner.cpp"):
-        with open(os.path.join(ROOT, "paper_2009_10955_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2009_10955_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

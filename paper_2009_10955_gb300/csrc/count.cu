@@ -21,7 +21,9 @@
 // the loop at depth k-2 gives one candidate to each lane, which counts the
 // last level alone (heavy candidates go back to the whole warp). The last
 // loop is never enumerated: its contribution is the size of its clipped
-// candidate set minus the already-matched vertices inside it.
+// candidate set minus the already-matched vertices inside it. Plans whose
+// later vertices all lie below v1 run, for tasks whose v1 is a core vertex,
+// on shared-memory bitmaps instead (the bitmap subtree below).
 //
 // Counts are accumulated per lane in 128 bits and reduced with warp shuffles;
 // one atomic pair (low word, carry into the high word) per warp per job
@@ -676,7 +678,8 @@ __device__ __forceinline__ void bitmap_last_two(const TaskCtx& c, int* v, int W,
     }
 }
 
-// Rank of a set bit of S (Ws words) for one lane, shared by the lane paths:
+// Rank of a set bit of S (Ws words) for one lane, as the three-level lane
+// tail uses it (the last-two lane path above runs the same scan inline):
 // lane l owns words [l per, (l + 1) per); `excl` is the number of set bits
 // in the words of lanes below l, `T` the total.
 struct RankScan {
@@ -1027,8 +1030,8 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
                 c.col = J.col;
                 c.core_bits = J.core_bits;
                 c.core_n = (use_core && J.core_bits) ? J.core_n : 0;
-                // one candidate per lane pays off when the last level runs
-                // below two bitmap loops (k >= 5); 4-vertex plans prefer a warp
+                // bitmap subtree: one candidate per lane (mode 1 or 2), and
+                // in mode 2 the three-level lane tail where the plan allows
                 c.lane_bitmap = bitmap_mode != 0;
                 c.lane_three = bitmap_mode == 2;
                 if (c.core_n == 0 || J.core_words > c.bm_stride) c.bm = nullptr;
