@@ -1,5 +1,6 @@
-"""The multi-GPU path's host logic on CPU: world-size-2 gloo ranks shard the
-edge tasks and sum partial counts exactly (the sharded path's one exchange).
+"""The multi-GPU path's host logic on CPU: world-size-2 and -3 gloo ranks
+shard the roots and sum partial counts exactly (the sharded path's one
+exchange).
 Partial counts come from the oracle's restricted enumeration per root range,
 so the test needs no GPU."""
 
@@ -44,8 +45,8 @@ def _rank_main(rank, world, port, q):
     dist.destroy_process_group()
 
 
-def test_two_rank_shard_and_exact_sum():
-    world = 2
+@pytest.mark.parametrize("world", [2, 3])
+def test_ranks_shard_and_sum_exactly(world):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
@@ -60,8 +61,8 @@ def test_two_rank_shard_and_exact_sum():
     s, d = er_edges(n, 900, seed=21)
     g = oracle.build_csr(n, s, d)
     expect = [oracle.count(named_pattern(x), g) for x in ("triangle", "house", "c4")]
-    expect.append(2 * (1 << 33) + ((1 << 32) - 1))
-    assert res[0] == res[1] == expect
+    expect.append(world * (1 << 33) + (world * (world - 1) // 2) * ((1 << 32) - 1))
+    assert all(res[r] == expect for r in range(world))
 
 
 def test_shard_ranges_partition():
