@@ -326,6 +326,50 @@ gp_status gp_list(gp_graph* g, const gp_schedules* s, int32_t idx, int64_t task_
 gp_status gp_count_noalloc(gp_graph* g, const gp_schedules* s, int32_t idx, void* stream,
                            uint64_t* out);
 
+/* -------------------------------------------------------------- directed */
+
+/* Directed patterns on directed graphs. The paper names directed patterns
+ * as an extension of the method (Section II-A) without defining them; the
+ * reading here: a directed pattern has arcs a -> b, an embedding is an
+ * injective map that sends every pattern arc to a graph arc (non-induced),
+ * and the count divides the number of such maps by |Aut(P)|, the
+ * arc-preserving permutations. Algorithm 1 (Section IV-A) runs on that
+ * group; where it returns no restriction set (directed cycles: their
+ * rotations have no usable 2-cycles) the count runs without restrictions
+ * and divides by |Aut(P)|. */
+typedef struct gp_dgraph gp_dgraph;
+typedef struct gp_dpattern gp_dpattern;
+
+/* Directed graph from m arcs src[i] -> dst[i] (int32, host memory, or device
+ * memory with GP_DEVICE_PTRS): loops dropped, repeated arcs kept once, out-
+ * and in-lists sorted. Ids outside [0, n) give GP_ERR_ARG. Synchronises
+ * `stream`; the inputs may be released on return. */
+gp_status gp_dgraph_create(const int32_t* src, const int32_t* dst, int64_t m, int32_t n, uint32_t flags,
+                           void* stream, gp_dgraph** out);
+/* n and the number of distinct arcs (either pointer may be NULL). */
+gp_status gp_dgraph_stats(const gp_dgraph* g, int64_t* n, int64_t* narcs);
+/* Copy the lists back (host buffers; out_ptr and in_ptr n + 1 entries,
+ * out_col and in_col narcs entries; any may be NULL). Synchronous. */
+gp_status gp_dgraph_copy(const gp_dgraph* g, int64_t* out_ptr, int32_t* out_col, int64_t* in_ptr,
+                         int32_t* in_col);
+void gp_dgraph_destroy(gp_dgraph* g);
+
+/* Directed pattern from a k x k row-major 0/1 matrix (adj[a * k + b] = 1:
+ * arc a -> b; host memory), 3 <= k <= 7, zero diagonal, weakly connected
+ * (else GP_ERR_PATTERN). Computes the arc-preserving automorphisms. */
+gp_status gp_dpattern_create(const uint8_t* adj, int32_t k, gp_dpattern** out);
+gp_status gp_dpattern_aut_count(const gp_dpattern* p, uint64_t* out);
+void gp_dpattern_destroy(gp_dpattern* p);
+
+/* Count the embeddings of p in g. order == NULL: the configuration the
+ * performance model ranks first for the underlying undirected pattern
+ * (Section IV-C). Else order (k pattern vertices; every prefix weakly
+ * connected) with n_restr restrictions restr[2r] > restr[2r+1]: a valid set
+ * of Algorithm 1 (else GP_ERR_PATTERN), or none (n_restr = 0; the count
+ * then divides by |Aut(P)|). Writes *out on GP_OK; synchronises `stream`. */
+gp_status gp_dcount(const gp_dgraph* g, gp_dpattern* p, const int32_t* order, const int32_t* restr,
+                    int32_t n_restr, void* stream, uint64_t* out);
+
 /* ------------------------------------------------------------------ misc */
 
 const char* gp_status_str(gp_status s);

@@ -62,6 +62,14 @@ SIGNATURES = {
     "gp_count_scratch_bytes": (i32, [P, P, i32, P, P]),
     "gp_count_noalloc": (i32, [P, P, i32, P, P]),
     "gp_list": (i32, [P, P, i32, i64, i64, P, i64, P, P, P]),
+    "gp_dgraph_create": (i32, [P, P, i64, i32, u32, P, P]),
+    "gp_dgraph_stats": (i32, [P, P, P]),
+    "gp_dgraph_copy": (i32, [P, P, P, P, P]),
+    "gp_dgraph_destroy": (None, [P]),
+    "gp_dpattern_create": (i32, [P, i32, P]),
+    "gp_dpattern_aut_count": (i32, [P, P]),
+    "gp_dpattern_destroy": (None, [P]),
+    "gp_dcount": (i32, [P, P, P, P, i32, P, P]),
     "gp_status_str": (ctypes.c_char_p, [i32]),
     "gp_last_error": (ctypes.c_char_p, []),
     "gp_take_launch_count": (i64, []),
@@ -285,6 +293,43 @@ def gp_list(graph, schedules, idx, task_begin, task_end, out, capacity, stream=N
     return st, nw.value, nt.value
 
 
+def gp_dgraph_create(src, dst, n, flags=0, stream=None):
+    """Directed graph of arcs src[i] -> dst[i] (int32 numpy arrays, or device
+    tensors with GP_DEVICE_PTRS). Returns a DGraph."""
+    if isinstance(src, np.ndarray):
+        src = np.ascontiguousarray(src, dtype=np.int32)
+        dst = np.ascontiguousarray(dst, dtype=np.int32)
+    m = int(src.shape[0]) if hasattr(src, "shape") else len(src)
+    h = ctypes.c_void_p()
+    check(lib().gp_dgraph_create(_ptr(src), _ptr(dst), m, int(n), flags, _stream(stream), ctypes.byref(h)),
+          "gp_dgraph_create")
+    return DGraph(h)
+
+
+def gp_dpattern_create(adj):
+    """Directed pattern: adj[a, b] = 1 for an arc a -> b."""
+    adj = np.ascontiguousarray(adj, dtype=np.uint8)
+    if adj.ndim != 2 or adj.shape[0] != adj.shape[1]:
+        raise ValueError("adjacency must be k x k")
+    h = ctypes.c_void_p()
+    check(lib().gp_dpattern_create(_ptr(adj), adj.shape[0], ctypes.byref(h)), "gp_dpattern_create")
+    return DPattern(h, adj.shape[0])
+
+
+def gp_dcount(graph, pattern, order=None, restrictions=None, stream=None):
+    """Count; with order=None the planner chooses the configuration; with an
+    order, restrictions=[] counts without restrictions (dividing by |Aut|)."""
+    out = ctypes.c_uint64()
+    if order is None:
+        check(lib().gp_dcount(graph.h, pattern.h, None, None, 0, _stream(stream), ctypes.byref(out)), "gp_dcount")
+        return out.value
+    o = np.ascontiguousarray(order, dtype=np.int32)
+    res = np.ascontiguousarray(np.array(restrictions or [], dtype=np.int32).reshape(-1, 2))
+    check(lib().gp_dcount(graph.h, pattern.h, _ptr(o), _ptr(res) if res.size else None, res.shape[0],
+                          _stream(stream), ctypes.byref(out)), "gp_dcount")
+    return out.value
+
+
 def gp_take_launch_count():
     return int(lib().gp_take_launch_count())
 
@@ -393,3 +438,42 @@ class Schedules:
         return (tuple(int(x) for x in order[: self.k]),
                 tuple((int(res[2 * r]), int(res[2 * r + 1])) for r in range(nres.value)),
                 cost.value)
+
+
+class DGraph:
+    def __init__(self, h):
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.gp_dgraph_destroy(self.h)
+            self.h = None
+
+    def stats(self):
+        n, a = ctypes.c_int64(), ctypes.c_int64()
+        check(lib().gp_dgraph_stats(self.h, ctypes.byref(n), ctypes.byref(a)), "gp_dgraph_stats")
+        return {"n": n.value, "narcs": a.value}
+
+    def lists(self):
+        s = self.stats()
+        op, ip = np.zeros(s["n"] + 1, np.int64), np.zeros(s["n"] + 1, np.int64)
+        oc, ic = np.zeros(max(1, s["narcs"]), np.int32), np.zeros(max(1, s["narcs"]), np.int32)
+        check(lib().gp_dgraph_copy(self.h, _ptr(op), _ptr(oc), _ptr(ip), _ptr(ic)), "gp_dgraph_copy")
+        return op, oc[: s["narcs"]], ip, ic[: s["narcs"]]
+
+
+class DPattern:
+    def __init__(self, h, k):
+        self.h = h
+        self.k = k
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.gp_dpattern_destroy(self.h)
+            self.h = None
+
+    def aut_count(self):
+        out = ctypes.c_uint64()
+        check(lib().gp_dpattern_aut_count(self.h, ctypes.byref(out)), "gp_dpattern_aut_count")
+        return out.value
+

@@ -165,3 +165,26 @@ def test_labeled_pattern_groups(N):
     assert p.aut_count() == N.gp_pattern_create(adj).aut_count() == 8
     assert N.gp_pattern_create_labeled(adj, [0, 1, 0, 1]).aut_count() == 4
     assert N.gp_pattern_create_labeled(adj, [0, 1, 2, 3]).aut_count() == 1
+
+
+def test_directed_patterns_host_side(N):
+    """Directed patterns (host): arc-preserving groups against the oracle's,
+    and malformed matrices rejected."""
+    import oracle
+
+    def pat(k, arcs):
+        a = np.zeros((k, k), np.uint8)
+        for x, y in arcs:
+            a[x, y] = 1
+        return a
+    cases = [pat(3, [(0, 1), (1, 2), (2, 0)]), pat(3, [(0, 1), (0, 2), (1, 2)]),
+             pat(4, [(0, 1), (1, 2), (2, 3), (3, 0)]), pat(4, [(0, 2), (0, 3), (1, 2), (1, 3)]),
+             pat(4, [(0, 1), (0, 2), (0, 3)]), pat(3, [(0, 1), (1, 0), (0, 2), (1, 2)])]
+    for a in cases:
+        assert N.gp_dpattern_create(a).aut_count() == oracle.aut_count_directed(a)
+    for bad in (pat(3, [(0, 1)]),                              # not weakly connected
+                pat(2, [(0, 1)]),                              # too small
+                np.eye(3, dtype=np.uint8)):                    # loops
+        with pytest.raises(N.GraphPiError) as e:
+            N.gp_dpattern_create(bad)
+        assert e.value.status == N.GP_ERR_PATTERN
