@@ -14,8 +14,10 @@
  * sorted neighbour lists (Section IV-B, IV-E), pruned by asymmetric
  * restrictions id(a) > id(b) produced by 2-cycle automorphism elimination
  * (Algorithm 1, Section IV-A), with the configuration chosen by the
- * performance model of Section IV-C. The API takes "a pattern and a data
- * graph in the form of adjacency lists" (Section III).
+ * performance model of Section IV-C. As in the paper's overview (Section
+ * III), the inputs are a pattern and a data graph given as adjacency lists.
+ * Extensions below: vertex-labelled patterns, listing, inclusion-exclusion
+ * counting (Section IV-D) and directed patterns on directed graphs.
  *
  * Conventions for every call:
  *  - Return value: GP_OK (0) on success, GP_PARTIAL (> 0) for a count that
