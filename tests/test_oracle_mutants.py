@@ -35,6 +35,9 @@ MUTANTS = [
      "    u128 q = maps / (aut > 1 ? aut / 2 : aut);"),
     ("triangles_counted_twice", "                    if (c <= b) continue;\n", ""),
     ("ignores_graph_labels", "if (ok && w->glab && w->glab[v] != w->plab[d]) ok = 0;", ";"),
+    ("ignores_the_root_label", "if (w->glab && w->glab[img[0]] != w->plab[0]) continue;", ";"),
+    ("root_range_shifted", "img[0] = (int32_t)(w->root_begin + i * w->root_stride);",
+     "img[0] = (int32_t)(w->root_begin + i * w->root_stride - (i > 0));"),   # stays in range
     ("directed_ignores_arc_direction", "good = w->chk_fwd[d][c] ? arc_present(w, o, v) : arc_present(w, v, o);",
      "good = arc_present(w, o, v) || arc_present(w, v, o);"),
     ("directed_keeps_repeated_arcs", "if (uniq == 0 || fwd[i] != fwd[uniq - 1]) fwd[uniq++] = fwd[i];",
@@ -101,6 +104,10 @@ def battery():
         check("labels", oracle.count_labeled(named_pattern("c4"), [0, 1, 0, 1], bipartite(a, b), gl)
               == math.comb(a, 2) * math.comb(b, 2)
               and oracle.count_labeled(named_pattern("c4"), [0, 0, 1, 1], bipartite(a, b), gl) == 0)
+        # path a-b-c labelled 0, 1, 1 in K4 labelled 0, 1, 1, 1: the root is
+        # the one label-0 vertex, then 3 x 2 ordered label-1 vertices
+        path3 = np.array([[0, 1, 0], [1, 0, 1], [0, 1, 0]], np.uint8)
+        check("root_label", oracle.count_labeled(path3, [0, 1, 1], complete(4), [0, 1, 1, 1]) == 6)
         # directed: hand-worked lists, a transitive tournament, a complete digraph
         dg = oracle.build_dcsr(3, np.array([0, 1, 1, 0], np.int32), np.array([1, 0, 2, 1], np.int32))
         check("dcsr", list(dg.out_ptr) == [0, 1, 3, 3] and list(dg.out_col) == [1, 0, 2])
