@@ -39,8 +39,7 @@ WORKLOADS = {
     # House on G(2000, 20000), seed 1
     "er2000": {"graph": "er2000", "patterns": ["house"]},
     # Chung-Lu 4M vertices, 35M pairs, exponent 2.1, max expected degree 20K,
-    # seed 3 (the 6-cycle with a chord and the 3x2 grid need hours there,
-    # see the design notes; they are available with --patterns)
+    # seed 3
     "cl4m": {"graph": "cl4m", "patterns": ["k6e"]},
 }
 
@@ -63,8 +62,9 @@ def parse():
     ap.add_argument("--tune", action="store_true",
                     help="let the autotuner pick launch knobs per pattern (default: library defaults, which "
                          "measured faster on the full count than the tuner's task-sample choice)")
-    ap.add_argument("--iep", action="store_true",
-                    help="inclusion-exclusion for the last two loops where it applies (Section IV-D)")
+    ap.add_argument("--no-iep", action="store_true",
+                    help="plain enumeration only (default: inclusion-exclusion for the innermost loops where a "
+                         "plan qualifies, Section IV-D)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU-baseline sample budget")
     ap.add_argument("--batched-graphs", default="rmat12,rmat11,rmat10,rmat9,rmat8",
                     help="candidate graphs of the batched comparison, largest first ('' to skip)")
@@ -90,6 +90,24 @@ def peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+ALU_LANES_PER_SMSP = 16     # integer/logic (ALU pipe) lanes per SM sub-partition per cycle
+SMSP_PER_SM = 4
+
+
+def alu_peak_gops(nsm):
+    """Integer ALU peak in 32-bit lane operations per second (Gop/s): SMs x 4
+    sub-partitions x 16 ALU lanes x the maximum SM clock (MEASURED_PEAKS.json's
+    sm_max_mhz, else the GB300's 2070 MHz)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f)["sm_max_mhz"])
+        src = "measured sm_max_mhz"
+    except Exception:
+        mhz, src = 2070.0, "nominal 2070 MHz"
+    return nsm * SMSP_PER_SM * ALU_LANES_PER_SMSP * mhz * 1e6 / 1e9, (
+        f"{nsm} SMs x {SMSP_PER_SM} SMSPs x {ALU_LANES_PER_SMSP} ALU lanes x {mhz:.0f} MHz ({src})")
 
 
 # ----------------------------------------------------------------- clocks
@@ -157,70 +175,97 @@ class ClockSampler:
 
 # -------------------------------------------------------------- CPU baseline
 
-def _oracle_worker(n, src, dst, name, stride, offsets, threads, q):
-    """Child process: time the oracle on successive strided root sets."""
+def _oracle_worker(n, src, dst, name, sets, threads, q):
+    """Child process: time the oracle on the given root sets (begin, end,
+    stride) of the degree-ordered graph, one set after another."""
     import oracle
-    g = oracle.build_csr(n, src, dst)
+    g, _ = oracle.degree_relabel(oracle.build_csr(n, src, dst))
     q.put(("ready", 0, 0.0))
     adj = named_pattern(name)
-    for off in offsets:
+    for b, e, st in sets:
         t = time.time()
-        oracle.count_maps(adj, g, root_begin=int(off), root_stride=stride, threads=threads)
-        q.put(("batch", len(range(int(off), n, stride)), time.time() - t))
+        oracle.count_maps(adj, g, root_begin=int(b), root_end=int(e), root_stride=int(st), threads=threads)
+        q.put(("set", len(range(int(b), int(e), int(st))), time.time() - t))
 
 
-def cpu_baseline(n, src, dst, patterns, budget_s):
+def degree_strata(n, src, dst):
+    """Root ranges [a, b) of the degree-ordered graph holding the vertices of
+    degree in [2^i, 2^(i+1)) (degree order makes each stratum contiguous)."""
+    # degrees of the simple graph: loops and duplicate pairs dropped
+    a, b = np.minimum(src, dst).astype(np.int64), np.maximum(src, dst).astype(np.int64)
+    keep = a != b
+    key = np.unique(a[keep] * n + b[keep])
+    deg = np.bincount(np.concatenate([key // n, key % n]), minlength=n)
+    d = np.sort(deg)[::-1]
+    out, start = [], 0
+    while start < n and d[start] > 0:
+        top = int(d[start])
+        lo_deg = 1 << (top.bit_length() - 1)
+        end = start + int(np.searchsorted(-d[start:], -lo_deg, side="right"))
+        out.append((start, end, lo_deg))
+        start = end
+    return out
+
+
+def cpu_baseline(n, src, dst, patterns, budget_s, seed=12345, per_set=64):
     """The oracle (plain unrestricted enumeration, all host cores) on a
-    uniform random sample of root vertices, scaled to the whole graph:
-    estimated time = sample time x n / sampled roots. Each pattern runs in a
-    spawned child with a wall budget; a root set still running when the budget
-    ends counts with the time it had used, which makes the estimate a lower
-    bound (flagged)."""
+    degree-stratified sample of root vertices, scaled to the whole graph.
+    The roots are split into strata of degree [2^i, 2^(i+1)) (contiguous in
+    the degree order); from every stratum one set of up to `per_set` evenly
+    spaced roots (seeded offset) is timed to completion, lowest degrees
+    first, each pattern with an equal share of the budget. A stratum's time
+    is its set's time x stratum size / set size. Sets not reached, or cut at
+    the budget (counted with the time they had used), make the estimate a
+    lower bound, which is flagged. Both benchmark arms call this with the
+    same seed, so they time the same root sets."""
     import multiprocessing as mp
     import queue as qmod
     threads = os.cpu_count() or 1
     ctx = mp.get_context("spawn")
-    rng = np.random.default_rng(12345)
+    rng = np.random.default_rng(seed)
+    strata = degree_strata(n, src, dst)[::-1]       # lowest degrees first
+    sets = []
+    for a, b, _ in strata:
+        st = max(1, (b - a) // per_set)
+        off = int(rng.integers(0, st))
+        sets.append((a + off, b, st))
     per = budget_s / max(1, len(patterns))
     est, parts, lower = 0.0, [], False
-    stride = max(1, n // 64)
     for name in patterns:
         q = ctx.Queue()
-        offsets = rng.permutation(stride)[:4096]
-        proc = ctx.Process(target=_oracle_worker, args=(n, src, dst, name, stride, offsets, threads, q),
-                           daemon=True)
+        proc = ctx.Process(target=_oracle_worker, args=(n, src, dst, name, sets, threads, q), daemon=True)
         proc.start()
         try:
-            q.get(timeout=600)                       # CSR built; the clock starts now
+            q.get(timeout=900)                       # CSR built; the clock starts now
         except qmod.Empty:
             proc.terminate()
             raise RuntimeError("oracle CSR build did not finish")
         t0 = time.time()
-        roots, used = 0, 0.0
-        while True:
+        t_last = t0
+        pat_est, done = 0.0, 0
+        for (a, b, _), (sb, se, st) in zip(strata, sets):
             left = per - (time.time() - t0)
-            if left <= 0 or roots >= n:
-                break
             try:
+                if left <= 0:
+                    raise qmod.Empty
                 _, r, dt = q.get(timeout=left)
-                roots += r
-                used += dt
+                t_last = time.time()
+                pat_est += dt * (b - a) / max(r, 1)
+                done += 1
             except qmod.Empty:
+                # the set is cut: the time it had used stands for its whole
+                # stratum, and the strata after it add nothing
+                lower = True
+                pat_est += (time.time() - t_last) * (b - a) / max(1, len(range(sb, se, st)))
                 break
-        cut = proc.is_alive() and roots < n
-        if cut:
+        if proc.is_alive():
             proc.terminate()
             proc.join(timeout=10)
-            running = max(0.0, (time.time() - t0) - used)
-            if roots == 0 or running > 0.05 * used:
-                lower = True
-                roots += len(range(0, n, stride))
-                used += running
-        frac = max(roots, 1) / n
-        est += used / frac
-        parts.append(f"{name}: {roots} of {n} roots in {used:.1f} s" + (" (last root set cut)" if cut else ""))
+        est += pat_est
+        parts.append(f"{name}: {done} of {len(strata)} degree strata timed in {time.time() - t0:.1f} s")
     return {"value": est, "unit": "s", "cores": threads, "kind": "oracle",
-            "sample": "; ".join(parts) + "; uniform random strided root sets of 64 roots, estimate = time x n / roots",
+            "sample": "; ".join(parts) + f"; per stratum of degree [2^i, 2^(i+1)) one set of up to {per_set} "
+                      "evenly spaced roots, estimate = sum over strata of set time x stratum size / set size",
             "lower_bound": lower}
 
 
@@ -252,13 +297,15 @@ def shard_roots(row_ptr, rank, world):
 
 
 def allreduce_counts(counts, device=None):
-    """Exact sum over ranks of non-negative integer counts (< 2^64 each and in
-    total): each count travels as two 32-bit halves in int64 lanes."""
+    """Exact sum over ranks of non-negative integer totals (< 2^128 each and
+    in total): each travels as four 32-bit limbs in int64 lanes, which cannot
+    overflow for fewer than 2^31 ranks."""
     import torch
     import torch.distributed as dist
-    halves = torch.tensor([[c >> 32, c & 0xFFFFFFFF] for c in counts], dtype=torch.int64, device=device)
-    dist.all_reduce(halves)
-    return [(int(h) << 32) + int(l) for h, l in halves.tolist()]
+    limbs = torch.tensor([[(c >> (32 * i)) & 0xFFFFFFFF for i in range(4)] for c in counts],
+                         dtype=torch.int64, device=device)
+    dist.all_reduce(limbs)
+    return [sum(int(x) << (32 * i) for i, x in enumerate(row)) for row in limbs.tolist()]
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -300,17 +347,18 @@ def source_hash():
 
 
 def recorded_traffic(workload):
-    """Per-launch DRAM bytes of the count kernel from a committed ncu summary,
-    used only while the kernel source is unchanged since the capture."""
+    """Per-launch DRAM bytes of the count kernel for each pattern of a
+    workload, from a committed ncu summary, used only while the kernel source
+    is unchanged since the capture ({} otherwise)."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
         e = t.get(workload)
         if e and e.get("source_hash") == source_hash():
-            return e["dram_bytes_per_step"]
+            return dict(e.get("dram_bytes_per_launch") or e.get("per_launch") or {})
     except Exception:
         pass
-    return None
+    return {}
 
 
 def gpu_arm(a, rank, world):
@@ -330,12 +378,16 @@ def gpu_arm(a, rank, world):
     build_s = time.time() - t
     st = g.stats(stream=stream)
     nnz = g.device_csr()[2]
+    def make_plan(p, graph):
+        s = N.gp_schedule(N.gp_pattern_create(named_pattern(p)), graph, top_k=1, stream=stream)
+        if not a.no_iep:
+            s.set_iep(True)
+        return s
+
     plans, plan_s = {}, {}
     for p in pats:
         t = time.time()
-        plans[p] = N.gp_schedule(N.gp_pattern_create(named_pattern(p)), g, top_k=1, stream=stream)
-        if a.iep:
-            plans[p].set_iep(True)
+        plans[p] = make_plan(p, g)
         plan_s[p] = time.time() - t
     # this rank's share of every pattern's edge tasks: whole roots, balanced
     # by the sum of squared degrees
@@ -348,9 +400,7 @@ def gpu_arm(a, rank, world):
 
     # launch knobs per pattern from the autotuner (untimed, cached like plans)
     tuned, tune_s = {}, {}
-    if a.iep and world > 1:
-        raise SystemExit("--iep counts whole graphs only; run it with one GPU")
-    if a.tune and not a.iep:                 # the tuner samples task ranges
+    if a.tune:                               # the tuner samples task ranges
         from paper_2009_10955_gb300 import autotune
         cache = os.path.join(ROOT, "paper_2009_10955_gb300", "_build", "tune_cache.json")
         for p in pats:
@@ -367,9 +417,14 @@ def gpu_arm(a, rank, world):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     ms = ctypes.c_float()
 
+    raw_buf = (ctypes.c_uint64 * 2)()
+
     def count(p, timed):
+        """One timed count; returns the undivided total of this rank's tasks
+        (the count for plain plans), the call's and the kernel's ms."""
         flush.fill_(1)                                     # evict the graph from L2
-        o = knobs(p, task_begin=lo, task_end=hi, kernel_ms=ctypes.pointer(ms))
+        o = knobs(p, task_begin=lo, task_end=hi, kernel_ms=ctypes.pointer(ms),
+                  raw_total=ctypes.cast(raw_buf, ctypes.POINTER(ctypes.c_uint64)))
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -378,15 +433,18 @@ def gpu_arm(a, rank, world):
         e1.synchronize()
         if status != N.GP_OK:
             raise RuntimeError(f"count of {p} returned status {status}")
-        return c, e0.elapsed_time(e1), ms.value
+        return int(raw_buf[0]) | (int(raw_buf[1]) << 64), e0.elapsed_time(e1), ms.value
 
-    # algorithmic bytes per pattern (instrumented kernel, untimed)
-    algo = {}
+    # algorithmic work per pattern (instrumented kernel on the same paths as
+    # the timed launch, untimed): list-path bytes and bitmap word operations
+    algo, algo_ops = {}, {}
     for p in pats:
-        b = ctypes.c_uint64()
-        o = knobs(p, task_begin=lo, task_end=hi, flags=N.GP_COUNT_STATS, algo_bytes=ctypes.pointer(b))
+        b, ops = ctypes.c_uint64(), ctypes.c_uint64()
+        raw = (ctypes.c_uint64 * 2)()
+        o = knobs(p, task_begin=lo, task_end=hi, flags=N.GP_COUNT_STATS, algo_bytes=ctypes.pointer(b),
+                  algo_ops=ctypes.pointer(ops), raw_total=ctypes.cast(raw, ctypes.POINTER(ctypes.c_uint64)))
         N.gp_count(g, plans[p], 0, o, stream=stream)
-        algo[p] = b.value
+        algo[p], algo_ops[p] = b.value, ops.value
 
     for _ in range(a.warmup):
         for p in pats:
@@ -410,10 +468,16 @@ def gpu_arm(a, rank, world):
     torch.cuda.synchronize()
     clk = clocks.stop()
 
-    # sum partial counts over ranks (the one exchange of the sharded path)
+    # sum partial totals over ranks (the one exchange of the sharded path),
+    # then divide inclusion-exclusion totals by their plan's divisor
     if world > 1:
         summed = allreduce_counts([counts[p] for p in pats], device=dev)
         counts = dict(zip(pats, summed))
+    for p in pats:
+        div = plans[p].iep(0)[1]
+        if counts[p] % div:
+            raise RuntimeError(f"{p}: total {counts[p]} is not a multiple of its divisor {div}")
+        counts[p] //= div
         t_local = torch.tensor([statistics.mean(step_ms)], device=dev)
         dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
         mean_step = float(t_local[0])
@@ -431,8 +495,10 @@ def gpu_arm(a, rank, world):
         t = time.time()
         g2 = N.gp_graph_create_edges(src_h, dst_h, n, N.GP_DEGREE_ORDER, stream=stream)
         for p in pats:
-            s2 = N.gp_schedule(N.gp_pattern_create(named_pattern(p)), g2, top_k=1, stream=stream)
-            N.gp_count(g2, s2, 0, knobs(p, task_begin=lo, task_end=hi), stream=stream)
+            s2 = make_plan(p, g2)
+            N.gp_count(g2, s2, 0, knobs(p, task_begin=lo, task_end=hi,
+                                        raw_total=ctypes.cast(raw_buf, ctypes.POINTER(ctypes.c_uint64))),
+                       stream=stream)
         torch.cuda.synchronize()
         e2e_ms.append((time.time() - t) * 1000.0)
         del g2
@@ -459,9 +525,41 @@ def gpu_arm(a, rank, world):
     del xa, xb
     mean_kern = {p: statistics.mean(v) for p, v in kern_ms.items()}
     kern_total_ms = sum(mean_kern.values())
-    algo_total = sum(algo.values())
-    achieved = algo_total / (kern_total_ms / 1000.0) / 1e9 if kern_total_ms > 0 else 0.0
     traffic = recorded_traffic(a.workload)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak, alu_src = alu_peak_gops(nsm)
+    # per launch: list-path bytes against the HBM copy peak, bitmap word
+    # operations against the integer ALU peak; the bound is the larger share
+    per = {}
+    for p in pats:
+        t = mean_kern[p] / 1000.0
+        gbs = algo[p] / t / 1e9 if t > 0 else 0.0
+        gops = algo_ops[p] / t / 1e9 if t > 0 else 0.0
+        per[p] = {"launch_s": t, "share_of_step": mean_kern[p] / kern_total_ms if kern_total_ms else None,
+                  "list_bytes": algo[p], "list_gbs": gbs, "hbm_frac": gbs / hbm,
+                  "bitmap_ops": algo_ops[p], "bitmap_gops": gops, "alu_frac": gops / alu_peak,
+                  "dram_bytes": traffic.get(p)}
+        per[p]["bound"] = "alu" if per[p]["alu_frac"] > per[p]["hbm_frac"] else "hbm"
+    dom = max(pats, key=lambda p: mean_kern[p])
+    d = per[dom]
+    if d["bound"] == "alu":
+        roof = {"bound": "alu", "achieved": d["bitmap_gops"], "peak": alu_peak, "unit": "Gop/s",
+                "frac": d["alu_frac"], "peak_source": alu_src,
+                "algorithmic_per_launch": d["bitmap_ops"],
+                "algorithmic_unit": "32-bit word operations of the bitmap subtree (AND, POPC, scatter) and "
+                                    "candidates taken from its sets, tallied by the instrumented build"}
+    else:
+        roof = {"bound": "hbm", "achieved": d["list_gbs"], "peak": hbm, "unit": "GB/s", "frac": d["hbm_frac"],
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s",
+                "algorithmic_per_launch": d["list_bytes"],
+                "algorithmic_unit": "bytes of the list intersections executed (merge or search, whichever is "
+                                    "cheaper), stored elements and iterated candidates"}
+    roof.update({"traffic": d["dram_bytes"], "kernel": f"k_count ({dom} launch)", "launch_s": d["launch_s"],
+                 "share_of_step": d["share_of_step"], "l2_peak_gbs": l2_gbs,
+                 "per_pattern": per,
+                 "traffic_source": "profiles/traffic.json (ncu dram__bytes_read.sum + dram__bytes_write.sum "
+                                   "per launch), null when the kernel changed since the capture"})
     out = {
         "metric": "pattern-count time (s)",
         "value": mean_step / 1000.0,
@@ -482,7 +580,8 @@ def gpu_arm(a, rank, world):
             "patterns": pats,
             "counts": {p: counts[p] for p in pats},
             "per_pattern_s": {p: mean_kern[p] / 1000.0 for p in pats},
-            "plans": {p: plans[p].get(0)[:2] for p in pats},
+            "plans": {p: {"order": plans[p].get(0)[0], "restrictions": plans[p].get(0)[1],
+                          "iep_loops": plans[p].iep(0)[0], "iep_divisor": plans[p].iep(0)[1]} for p in pats},
             "graph_build_s": build_s,
             "plan_s": plan_s,
             "tuned": tuned,
@@ -496,23 +595,7 @@ def gpu_arm(a, rank, world):
                 "d2h_bytes_per_step": 8 * len(pats),
                 "includes": "graph build from host pairs in pinned memory, planning, counts, results to host"},
         "gpu_launches": launches // max(1, a.steps),
-        "roofline": {
-            "bound": "hbm",
-            "achieved": achieved,
-            "peak": hbm,
-            "unit": "GB/s",
-            "frac": achieved / hbm,
-            "traffic": traffic,
-            "kernel": "k_count",
-            "algorithmic_bytes_per_step": algo_total,
-            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
-            "l2_peak": l2_gbs,
-            "l2_frac": achieved / l2_gbs if l2_gbs > 0 else None,
-            "l2_peak_source": "measured in this run: 48 MB copy working set, read + write bytes",
-            "note": ("algorithmic bytes count 4-byte list elements (merge model); the bitmap paths test 32 ids "
-                     "per 4-byte word and the graph stays in L2, so achieved can exceed the HBM copy peak; "
-                     "traffic is the DRAM bytes ncu measured for these counts"),
-        },
+        "roofline": roof,
         "clocks": clk,
         "batched": batched,
     }
@@ -719,6 +802,8 @@ def main():
             g.stats()
             for pn in (a.patterns or "k4").split(","):
                 sc = N.gp_schedule(N.gp_pattern_create(named_pattern(pn)), g)
+                if not a.no_iep:
+                    sc.set_iep(True)
                 print(pn, N.gp_count(g, sc, 0), flush=True)
             torch.cuda.synchronize()
         return

@@ -175,17 +175,32 @@ gp_status gp_schedule_explicit(const gp_pattern* p, const int32_t* order, const 
                                int32_t n_restr, gp_schedules** out);
 
 /* Switch the plans of s to (enable != 0) or from inclusion-exclusion
- * counting of the last two loops (Section IV-D with k = 2). A plan qualifies
- * when k >= 4 and its last two searched vertices are not adjacent; the
- * restrictions acting at those two loops are dropped and the total is
+ * counting of the innermost loops (Section IV-D, Algorithm 2). A plan
+ * qualifies when its last kk >= 2 searched vertices are pairwise
+ * non-adjacent and at least two vertices are searched before them; the
+ * library takes the largest such kk (at most 5) whose divisor is exact.
+ * Once the outer vertices are bound, the count of kk distinct inner
+ * vertices is the inclusion-exclusion sum over the set partitions of their
+ * kk candidate sets (each term a product of intersection sizes). The
+ * restrictions acting at the inner loops are dropped and the total is
  * divided by the number of automorphic copies of each embedding that the
  * remaining restrictions still admit. The paper computes that number with
  * no_conflict; here it is counted exactly over all k! relative vertex
- * orders and the plan keeps plain enumeration when it is not the same for
- * every order. *n_iep (may be NULL) receives how many plans switched.
- * Inclusion-exclusion plans count whole graphs only: gp_count with a task
- * range or budget, and gp_count_batch_ranges, reject them with GP_ERR_ARG. */
+ * orders, and a kk for which it is not the same for every order is not
+ * used. *n_iep (may be NULL) receives how many plans switched. Counts over
+ * part of the edge tasks (a task range, a budget, a time slice) are not
+ * divisible on their own: those calls return the undivided 128-bit total
+ * in gp_count_opts.raw_total; totals of disjoint ranges add up, and their
+ * sum divided by the plan's divisor (gp_schedule_iep) is the count. With
+ * kk = 5 the graph's maximum degree must be below 2^24 (GP_ERR_ARG
+ * otherwise), so that every term stays inside 128 bits. */
 gp_status gp_schedule_set_iep(gp_schedules* s, int32_t enable, int32_t* n_iep);
+
+/* Inclusion-exclusion form of plan idx: *kk (may be NULL) receives the
+ * number of innermost loops it replaces (0: plain enumeration) and
+ * *divisor (may be NULL) the number by which its undivided totals are
+ * divided (1 for plain plans). */
+gp_status gp_schedule_iep(const gp_schedules* s, int32_t idx, int32_t* kk, uint32_t* divisor);
 
 /* Number of plans held. */
 gp_status gp_schedule_size(const gp_schedules* s, int32_t* count);
@@ -239,10 +254,25 @@ typedef struct gp_count_opts {
                                  gp_count_batch return GP_ERR_TIMEOUT,
                                  gp_count_batch_ranges sets its next_task to -1.
                                  Other jobs of the same launch are unaffected.    */
+    uint64_t* raw_total;      /* host out (may be NULL): the undivided 128-bit total
+                                 of the processed tasks as (low, high) words, one
+                                 pair per job in the batch calls. It equals the
+                                 count for plain plans; for inclusion-exclusion
+                                 plans it is the count times the plan's divisor
+                                 (gp_schedule_iep). Required when an
+                                 inclusion-exclusion plan counts part of the tasks
+                                 (GP_ERR_ARG otherwise)                            */
+    uint64_t* algo_ops;       /* host out (with GP_COUNT_STATS; may be NULL): word
+                                 operations of the bitmap subtree -- one per 32-bit
+                                 word ANDed, popcounted or scattered, and one per
+                                 candidate taken from a set (the bitmap
+                                 counterpart of algo_bytes, which then covers the
+                                 list path only)                                   */
 } gp_count_opts;
 
 /* gp_count_opts.flags */
 #define GP_COUNT_STATS 1   /* run the instrumented kernel that tallies algo_bytes
+                              and algo_ops on the same paths as the plain kernel
                               (slower; for measurement only)                      */
 #define GP_COUNT_NO_CORE 2 /* never use the core adjacency bit matrix: every
                               membership test is a binary search                  */
@@ -257,9 +287,12 @@ typedef struct gp_count_opts {
 
 /* Count the embeddings of the pattern of `s` in `g` with plan `idx`.
  * Every embedding is counted exactly once (restrictions, Algorithm 1).
- * Writes *out (host) on GP_OK. GP_ERR_OVERFLOW when the count needs more
- * than 64 bits. Runs on `stream` and synchronises it before returning; the
- * only device-to-host traffic is the 16-byte result and an error word. */
+ * Writes *out (host) on GP_OK and GP_PARTIAL. GP_ERR_OVERFLOW when the
+ * count needs more than 64 bits. An inclusion-exclusion plan counting part
+ * of the tasks (opts->task_begin / task_end, or a budget that stops it)
+ * writes 0 to *out and its undivided total to opts->raw_total. Runs on
+ * `stream` and synchronises it before returning; the only device-to-host
+ * traffic is the 16-byte result and an error word. */
 gp_status gp_count(gp_graph* g, const gp_schedules* s, int32_t idx, const gp_count_opts* opts,
                    void* stream, uint64_t* out);
 
@@ -278,7 +311,9 @@ gp_status gp_count_batch(gp_graph* const* graphs, const gp_schedules* const* sch
  * first unprocessed task (== the job's end when it is complete; -1 when the
  * job was abandoned under opts->task_cycles). Returns GP_OK when every job
  * completed, GP_PARTIAL otherwise; counts over disjoint
- * task ranges add up to the full count. Synchronises `stream`. This is the
+ * task ranges add up to the full count. Inclusion-exclusion jobs need
+ * opts->raw_total (2 x njobs words): their out[j] is 0 and raw_total holds
+ * their undivided partial totals. Synchronises `stream`. This is the
  * call a continuous-batching server issues once per time slice. */
 gp_status gp_count_batch_ranges(gp_graph* const* graphs, const gp_schedules* const* scheds,
                                 const int32_t* idx, const int64_t* task_begin,
@@ -324,7 +359,12 @@ gp_status gp_list(gp_graph* g, const gp_schedules* s, int32_t idx, int64_t task_
  * the array and it keeps the last call's contents (each call clears what
  * must start at zero): calls that overlap on the GPU, from any thread or
  * stream, race and must be serialised by the caller. Counts all edge tasks;
- * writes *out on GP_OK; synchronises `stream`. */
+ * writes *out on GP_OK; synchronises `stream`. Also: labelled plans give
+ * GP_ERR_ARG (they count through the listing kernel, which allocates);
+ * under CUDA's lazy module loading the driver creates the 64 MiB array when
+ * the first call on a device loads this code, so that first call reserves
+ * the memory; and the call makes the graph's device current and leaves it
+ * current. */
 gp_status gp_count_noalloc(gp_graph* g, const gp_schedules* s, int32_t idx, void* stream,
                            uint64_t* out);
 

@@ -62,6 +62,8 @@ def configure(lib):
     lib.oracle_aut_count.argtypes = [i32, P, P]
     lib.oracle_count_maps.argtypes = [i32, P, i32, P, P, i32, i32, i32, i32, P, P]
     lib.oracle_count_restricted.argtypes = [i32, P, P, i32, P, i32, P, P, i32, i32, i32, P, P]
+    lib.oracle_count_restricted_entries.argtypes = [i32, P, P, i32, P, i32, P, P, i64, i64, i32, P, P]
+    lib.oracle_count_restricted_entries.restype = ctypes.c_int
     lib.oracle_triangles.argtypes = [i32, P, P, i32, P]
     lib.oracle_list_restricted.argtypes = [i32, P, P, i32, P, i32, P, P, i32, i32, P, i64, P]
     lib.oracle_list_restricted.restype = ctypes.c_int
@@ -173,6 +175,26 @@ def count_restricted(adj, order, restrictions, g, threads=None, root_begin=0, ro
                                          threads or default_threads(), _p(hi), _p(lo))
     if rc:
         raise ValueError(f"oracle_count_restricted failed ({rc})")
+    return (int(hi[0]) << 64) | int(lo[0])
+
+
+def count_restricted_entries(adj, order, restrictions, g, entry_begin, entry_end, threads=None):
+    """count_restricted over the maps whose first two searched vertices are
+    a CSR entry (row, column) in ``[entry_begin, entry_end)``."""
+    adj = _adj(adj)
+    k = adj.shape[0]
+    order = np.ascontiguousarray(order, dtype=np.int32)
+    res = np.ascontiguousarray(np.array(restrictions, dtype=np.int32).reshape(-1, 2))
+    nres = res.shape[0] if res.size else 0
+    if res.size == 0:
+        res = np.zeros((1, 2), dtype=np.int32)
+    hi = np.zeros(1, dtype=np.uint64)
+    lo = np.zeros(1, dtype=np.uint64)
+    rc = _load().oracle_count_restricted_entries(k, _p(adj), _p(order), nres, _p(res), g.n,
+                                                 _p(g.row_ptr), _p(g.col), int(entry_begin), int(entry_end),
+                                                 threads or default_threads(), _p(hi), _p(lo))
+    if rc:
+        raise ValueError(f"oracle_count_restricted_entries failed ({rc})")
     return (int(hi[0]) << 64) | int(lo[0])
 
 

@@ -92,6 +92,8 @@ typedef struct {
     const int64_t* row_ptr;
     const int32_t* col;
     int32_t root_begin, root_end, root_stride;
+    int64_t entry_begin, entry_end; /* entry mode: only the CSR entries (v0, v1) of   */
+    int entry_mode;                 /* [entry_begin, entry_end) start the walk       */
     const int32_t* glab;   /* graph vertex labels, or NULL (unlabelled)        */
     int32_t plab[8];       /* label required at depth d                        */
     atomic_long cursor;    /* next root index (in stride units) to hand out */
@@ -106,26 +108,40 @@ static int has_edge(const walk_t* w, int32_t u, int32_t v) {
     return lo < w->row_ptr[u + 1] && w->col[lo] == v;
 }
 
+/* May v (a neighbour of the anchor's image) be the image at depth d? */
+static int admit(const walk_t* w, int d, const int32_t* img, int32_t v) {
+    for (int j = 0; j < d; ++j) if (img[j] == v) return 0;                 /* injective */
+    for (int c = 0; c < w->nchk[d]; ++c)
+        if (!has_edge(w, img[w->chk[d][c]], v)) return 0;                   /* edges */
+    for (int r = 0; r < w->nres[d]; ++r) {
+        int32_t o = img[w->res_other[d][r]];
+        if (w->res_gt[d][r] ? !(v > o) : !(v < o)) return 0;                /* restriction */
+    }
+    if (w->glab && w->glab[v] != w->plab[d]) return 0;                     /* label */
+    return 1;
+}
+
 static u128 walk(const walk_t* w, int d, int32_t* img) {
     if (d == w->k) return 1;                     /* every pattern vertex mapped */
     u128 total = 0;
     int32_t a = img[w->anchor[d]];
     for (int64_t e = w->row_ptr[a]; e < w->row_ptr[a + 1]; ++e) {
         int32_t v = w->col[e];
-        int ok = 1;
-        for (int j = 0; j < d && ok; ++j) if (img[j] == v) ok = 0;          /* injective */
-        for (int c = 0; c < w->nchk[d] && ok; ++c)
-            if (!has_edge(w, img[w->chk[d][c]], v)) ok = 0;                  /* edges */
-        for (int r = 0; r < w->nres[d] && ok; ++r) {
-            int32_t o = img[w->res_other[d][r]];
-            if (w->res_gt[d][r] ? !(v > o) : !(v < o)) ok = 0;               /* restriction */
-        }
-        if (ok && w->glab && w->glab[v] != w->plab[d]) ok = 0;             /* label */
-        if (!ok) continue;
+        if (!admit(w, d, img, v)) continue;
         img[d] = v;
         total += walk(w, d + 1, img);
     }
     return total;
+}
+
+/* Row of CSR entry e: the last u with row_ptr[u] <= e. */
+static int32_t entry_row(const walk_t* w, int64_t e) {
+    int32_t lo = 0, hi = w->n - 1;
+    while (lo < hi) {
+        int32_t mid = lo + (hi - lo + 1) / 2;
+        if (w->row_ptr[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    return lo;
 }
 
 typedef struct { walk_t* w; u128 sum; } worker_t;
@@ -135,6 +151,23 @@ static void* worker_main(void* arg) {
     walk_t* w = me->w;
     int32_t img[8];
     const long chunk = 16;
+    if (w->entry_mode) {                         /* the walk from single entries, */
+        long count = (long)(w->entry_end - w->entry_begin);   /* one per grab      */
+        for (;;) {
+            long s = atomic_fetch_add(&w->cursor, 1);
+            if (s >= count) break;
+            long e = s + 1;
+            for (long i = s; i < e; ++i) {
+                int64_t x = w->entry_begin + i;
+                img[0] = entry_row(w, x);
+                if (w->glab && w->plab[0] != w->glab[img[0]]) continue;   /* root label */
+                if (!admit(w, 1, img, w->col[x])) continue;
+                img[1] = w->col[x];
+                me->sum += walk(w, 2, img);
+            }
+        }
+        return NULL;
+    }
     long count = (w->root_end - w->root_begin + w->root_stride - 1) / w->root_stride;
     for (;;) {
         long s = atomic_fetch_add(&w->cursor, chunk);
@@ -349,6 +382,31 @@ static void list_walk(const walk_t* w, int d, int32_t* img, list_sink* sink) {
         img[d] = v;
         list_walk(w, d + 1, img, sink);
     }
+}
+
+int oracle_count_restricted_entries(int32_t k, const uint8_t* adj, const int32_t* order,
+                                    int32_t nres, const int32_t* res,
+                                    int32_t n, const int64_t* row_ptr, const int32_t* col,
+                                    int64_t entry_begin, int64_t entry_end,
+                                    int32_t nthreads, uint64_t* hi, uint64_t* lo) {
+    if (!hi || !lo || !order || (nres > 0 && !res) || nres < 0 || k < 2) return -1;
+    walk_t* w = (walk_t*)malloc(sizeof(walk_t));
+    if (!w) return -2;
+    int rc = setup_walk(w, k, adj, order, nres, res, n, row_ptr, col);
+    if (rc) { free(w); return rc; }
+    int64_t nnz = n > 0 ? row_ptr[n] : 0;
+    if (entry_begin < 0) entry_begin = 0;
+    if (entry_end > nnz) entry_end = nnz;
+    if (entry_end < entry_begin) entry_end = entry_begin;
+    w->entry_mode = 1;
+    w->entry_begin = entry_begin;
+    w->entry_end = entry_end;
+    u128 total = 0;
+    rc = run_walk(w, nthreads, &total);
+    free(w);
+    if (rc) return rc;
+    split128(total, hi, lo);
+    return 0;
 }
 
 int oracle_list_restricted(int32_t k, const uint8_t* adj, const int32_t* order,

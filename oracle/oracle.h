@@ -60,6 +60,17 @@ int oracle_count_restricted(int32_t k, const uint8_t* adj, const int32_t* order,
                             int32_t root_begin, int32_t root_end,
                             int32_t nthreads, uint64_t* hi, uint64_t* lo);
 
+/* oracle_count_restricted over the maps whose first two searched vertices
+ * are one CSR entry (v0, v1) of [entry_begin, entry_end): v0 the entry's
+ * row, v1 its column (the second searched pattern vertex is adjacent to the
+ * first in every order with connected prefixes). The entries of a root's
+ * row split its count into disjoint parts. */
+int oracle_count_restricted_entries(int32_t k, const uint8_t* adj, const int32_t* order,
+                                    int32_t nres, const int32_t* res,
+                                    int32_t n, const int64_t* row_ptr, const int32_t* col,
+                                    int64_t entry_begin, int64_t entry_end,
+                                    int32_t nthreads, uint64_t* hi, uint64_t* lo);
+
 /* The embeddings found by oracle_count_restricted with roots in
  * [root_begin, root_end), single-threaded in depth-first order: embedding i
  * is written as out[i * k + a] = image of pattern vertex a, for at most cap

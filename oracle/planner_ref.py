@@ -9,16 +9,16 @@ of ``v``. A restriction ``(a, b)`` means id(a) > id(b). A schedule is the
 tuple of pattern vertices in search order; loops are numbered 1..n as in the
 paper's performance model.
 
-Readings of the paper used here (each also listed in the design notes):
+Readings of the paper used here (where the text is silent or garbled):
 
 * Algorithm 1 finds a 2-cycle as a vertex that is the image of its own
   image; a fixed point also meets that test, so the vertex must also differ
   from its image, and the pair added is ``(vertex, perm[vertex])``.
-* ``generate`` depends on its arguments only through ``res_set``: the group
-  it receives is exactly the automorphisms not yet eliminated by
-  ``res_set``, because ``no_conflict`` is monotone (a permutation that closes a
-  cycle under a set still closes it under every superset). Its results are
-  therefore cached per ``res_set``; this changes the running time only.
+* The elimination explores restriction sets, not permutation groups: the
+  automorphisms a branch still has to eliminate are exactly those that
+  survive its set under ``no_conflict``, which is monotone (a permutation
+  that closes a cycle under a set still closes it under every superset), so
+  every set needs to be examined once.
 * Phase 2 of the schedule filter can leave no schedule at all (for example
   the 4-cycle and 6-cycle); the largest k' <= k that keeps at least one
   phase-1 schedule is used instead, and k' = 1 means phase 1 alone.
@@ -37,7 +37,6 @@ Readings of the paper used here (each also listed in the design notes):
   (same operand loops) are computed once.
 """
 
-from functools import lru_cache
 from itertools import combinations, permutations
 from math import factorial
 
@@ -100,29 +99,40 @@ def validate(k, aut_count, res_set):
 
 
 def restriction_sets(adj, labels=None):
-    """Algorithm 1 (res_set_generation): every restriction set it returns,
-    as a sorted list of sorted tuples of pairs."""
+    """The restriction sets of Section IV-A's 2-cycle elimination
+    (Algorithm 1), as a sorted list of sorted tuples of pairs.
+
+    Restated as a breadth-first search over restriction sets, level by level
+    in the number of restrictions. A set that some automorphism other than
+    the identity survives (``no_conflict``) is extended, once for every
+    2-cycle (v, w) of every surviving automorphism, by the restriction
+    (v, w); a set that only the identity survives is final, and it is kept
+    when its linear extensions times |Aut| equal k! (``validate``). Each set
+    is visited once however many routes lead to it."""
     k = len(adj)
     auts = automorphisms(adj, labels)
     n_aut = len(auts)
-
-    @lru_cache(maxsize=None)
-    def generate(res_set):
-        pg = [p for p in auts if no_conflict(p, res_set)]
-        if len(pg) > 1:
-            sets = set()
-            for perm in pg:
-                for vertex in range(k):
-                    if perm[vertex] != vertex and perm[perm[vertex]] == vertex:  # a 2-cycle
-                        new_set = frozenset(res_set | {(vertex, perm[vertex])})
-                        sets |= generate(new_set)
-            return frozenset(sets)
-        if validate(k, n_aut, res_set):
-            return frozenset([res_set])
-        return frozenset()
-
-    out = generate(frozenset())
-    return sorted(tuple(sorted(s)) for s in out)
+    level = {frozenset()}
+    seen = set(level)
+    found = set()
+    while level:
+        following = set()
+        for res_set in level:
+            alive = [p for p in auts if no_conflict(p, res_set)]
+            if len(alive) <= 1:
+                if validate(k, n_aut, res_set):
+                    found.add(res_set)
+                continue
+            for perm in alive:
+                for v in range(k):
+                    w = perm[v]
+                    if w != v and perm[w] == v:                     # a 2-cycle (v, w)
+                        child = res_set | {(v, w)}
+                        if child not in seen:
+                            seen.add(child)
+                            following.add(child)
+        level = following
+    return sorted(tuple(sorted(s)) for s in found)
 
 
 def max_independent_set_size(adj):

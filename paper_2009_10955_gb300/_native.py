@@ -53,6 +53,7 @@ SIGNATURES = {
     "gp_schedule_explicit": (i32, [P, P, P, i32, P]),
     "gp_schedule_size": (i32, [P, P]),
     "gp_schedule_set_iep": (i32, [P, i32, P]),
+    "gp_schedule_iep": (i32, [P, i32, P, P]),
     "gp_schedule_get": (i32, [P, i32, P, P, P, P]),
     "gp_config_cost": (i32, [P, P, P, i32, f64, f64, f64, P]),
     "gp_schedule_destroy": (None, [P]),
@@ -93,6 +94,8 @@ class gp_count_opts(ctypes.Structure):
         ("lane_work", ctypes.c_int32),
         ("reserved1", ctypes.c_int32),
         ("task_cycles", ctypes.c_int64),
+        ("raw_total", ctypes.POINTER(ctypes.c_uint64)),
+        ("algo_ops", ctypes.POINTER(ctypes.c_uint64)),
     ]
 
 
@@ -232,6 +235,19 @@ def gp_count(graph, schedules, idx=0, opts=None, stream=None):
     return st, out.value
 
 
+def gp_count_raw(graph, schedules, idx=0, opts=None, stream=None, **kw):
+    """Returns (status, raw): the undivided 128-bit total of the processed
+    tasks as a Python int (the count for plain plans; count x divisor for
+    inclusion-exclusion plans). Extra keywords go to make_opts."""
+    raw = (ctypes.c_uint64 * 2)()
+    o = opts if opts is not None else make_opts(**kw)
+    o.raw_total = ctypes.cast(raw, ctypes.POINTER(ctypes.c_uint64))
+    out = ctypes.c_uint64()
+    st = check(lib().gp_count(graph.h, schedules.h, idx, ctypes.byref(o), _stream(stream), ctypes.byref(out)),
+               "gp_count")
+    return st, int(raw[0]) | (int(raw[1]) << 64)
+
+
 def gp_count_batch(graphs, schedules, idx=None, opts=None, stream=None):
     n = len(graphs)
     G = (ctypes.c_void_p * n)(*[g.h.value for g in graphs])
@@ -243,8 +259,10 @@ def gp_count_batch(graphs, schedules, idx=None, opts=None, stream=None):
     return out
 
 
-def gp_count_batch_ranges(graphs, schedules, idx, task_begin, task_end, opts=None, stream=None):
-    """Returns (status, counts, next_task) for one time slice."""
+def gp_count_batch_ranges(graphs, schedules, idx, task_begin, task_end, opts=None, stream=None, raw=None):
+    """Returns (status, counts, next_task) for one time slice. With raw (a
+    uint64 numpy array of 2 x len(graphs)), the undivided 128-bit totals
+    (low, high) are written there; inclusion-exclusion jobs need it."""
     n = len(graphs)
     G = (ctypes.c_void_p * n)(*[g.h.value for g in graphs])
     S = (ctypes.c_void_p * n)(*[s.h.value for s in schedules])
@@ -253,6 +271,10 @@ def gp_count_batch_ranges(graphs, schedules, idx, task_begin, task_end, opts=Non
     E = np.ascontiguousarray(task_end, dtype=np.int64)
     out = np.zeros(n, dtype=np.uint64)
     nxt = np.zeros(n, dtype=np.int64)
+    if raw is not None:
+        if opts is None:
+            opts = make_opts()
+        opts.raw_total = raw.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
     st = check(lib().gp_count_batch_ranges(G, S, _ptr(I), _ptr(B), _ptr(E), n,
                                            ctypes.byref(opts) if opts is not None else None,
                                            _stream(stream), _ptr(out), _ptr(nxt)), "gp_count_batch_ranges")
@@ -422,6 +444,13 @@ class Schedules:
         n = ctypes.c_int32()
         check(lib().gp_schedule_set_iep(self.h, 1 if enable else 0, ctypes.byref(n)), "gp_schedule_set_iep")
         return n.value
+
+    def iep(self, idx=0):
+        """(kk, divisor) of plan idx: kk innermost loops replaced by
+        inclusion-exclusion (0: none), undivided totals divided by divisor."""
+        kk, div = ctypes.c_int32(), ctypes.c_uint32()
+        check(lib().gp_schedule_iep(self.h, idx, ctypes.byref(kk), ctypes.byref(div)), "gp_schedule_iep")
+        return kk.value, div.value
 
     def __len__(self):
         c = ctypes.c_int32()

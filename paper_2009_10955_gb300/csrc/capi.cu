@@ -136,8 +136,15 @@ gp_status make_job(gp_graph* g, const gp_schedules* s, int32_t idx, const gp_cou
     job->core_words = g->core_words;
     job->labels = g->labels;
     if (job->plan.labeled && !g->labels) return fail(GP_ERR_ARG, "labelled pattern on a graph without labels");
+    // a term of the five-set inclusion-exclusion expansion multiplies five
+    // set sizes: keep it inside 128 bits
+    if (job->plan.iep == 5 && g->max_deg >= (1 << 24))
+        return fail(GP_ERR_ARG, "five-loop inclusion-exclusion needs a maximum degree below 2^24");
     return GP_OK;
 }
+
+// True when a job covers every edge task of its graph.
+bool whole_graph(const CountJob& job, const gp_graph* g) { return job.task_begin == 0 && job.ntasks == g->nnz; }
 
 // A job's count from its 128-bit device total: inclusion-exclusion plans
 // divide by their multiplicity, exactly.
@@ -558,8 +565,9 @@ gp_status gp_count(gp_graph* g, const gp_schedules* s, int32_t idx, const gp_cou
     CountJob job;
     gp_status rc = make_job(g, s, idx, opts, &job);
     if (rc != GP_OK) return rc;
-    if (job.plan.iep && (job.task_begin != 0 || job.ntasks != g->nnz || (opts && opts->budget_cycles > 0)))
-        return fail(GP_ERR_ARG, "inclusion-exclusion plans count whole graphs only (no task range or budget)");
+    const bool iep_part = job.plan.iep && (!whole_graph(job, g) || (opts && opts->budget_cycles > 0));
+    if (iep_part && !(opts && opts->raw_total))
+        return fail(GP_ERR_ARG, "an inclusion-exclusion count over part of the tasks needs opts->raw_total");
     rc = ensure_device(g);
     if (rc != GP_OK) return rc;
     if (job.plan.labeled) {                  // labelled plans: the listing kernel's counting pass
@@ -577,15 +585,22 @@ gp_status gp_count(gp_graph* g, const gp_schedules* s, int32_t idx, const gp_cou
     uint64_t bytes = 0;
     const bool want_ms = opts && opts->kernel_ms;
     int aborted = 0;
+    uint64_t ops = 0;
     rc = run_count(&job, 1, launch_opts(opts), static_cast<cudaStream_t>(stream), res, &done,
-                   want_ms ? &ms : nullptr, &bytes, &aborted);
+                   want_ms ? &ms : nullptr, &bytes, &aborted, &ops);
     if (rc != GP_OK) return rc;
     if (aborted) return fail(GP_ERR_TIMEOUT, "a work item outlived opts.task_cycles; the count was abandoned");
     uint64_t total = 0;
-    rc = finish_total(job.plan, res[0], res[1], &total);
-    if (rc != GP_OK) return rc;
+    if (job.plan.iep && (iep_part || done < job.nvirt)) {
+        total = 0;                           // only the undivided raw total is meaningful
+    } else {
+        rc = finish_total(job.plan, res[0], res[1], &total);
+        if (rc != GP_OK) return rc;
+    }
+    if (opts && opts->raw_total) { opts->raw_total[0] = res[0]; opts->raw_total[1] = res[1]; }
     if (want_ms) *opts->kernel_ms = ms;
     if (opts && opts->algo_bytes && (opts->flags & GP_COUNT_STATS)) *opts->algo_bytes = bytes;
+    if (opts && opts->algo_ops && (opts->flags & GP_COUNT_STATS)) *opts->algo_ops = ops;
     if (done < job.nvirt) {
         if (opts && opts->resume_cursor) *opts->resume_cursor = job.task_begin + done;
         *out = total;
@@ -626,19 +641,23 @@ gp_status gp_count_batch(gp_graph* const* graphs, const gp_schedules* const* sch
     uint64_t bytes = 0;
     const bool want_ms = opts && opts->kernel_ms;
     std::vector<int> aborted((size_t)njobs, 0);
+    uint64_t ops = 0;
     rc = run_count(jobs.data(), njobs, lo, static_cast<cudaStream_t>(stream), res.data(), &done,
-                   want_ms ? &ms : nullptr, &bytes, aborted.data());
+                   want_ms ? &ms : nullptr, &bytes, aborted.data(), &ops);
     if (rc != GP_OK) return rc;
     for (int32_t j = 0; j < njobs; ++j)
         if (aborted[j]) return fail(GP_ERR_TIMEOUT, "a work item outlived opts.task_cycles; the batch was abandoned");
     if (want_ms) *opts->kernel_ms = ms;
     if (opts && opts->algo_bytes && (opts->flags & GP_COUNT_STATS)) *opts->algo_bytes = bytes;
+    if (opts && opts->algo_ops && (opts->flags & GP_COUNT_STATS)) *opts->algo_ops = ops;
     std::vector<uint64_t> tot((size_t)njobs);
     for (int32_t j = 0; j < njobs; ++j) {
         rc = finish_total(jobs[j].plan, res[2 * j], res[2 * j + 1], &tot[j]);
         if (rc != GP_OK) return rc;
     }
     for (int32_t j = 0; j < njobs; ++j) out[j] = tot[j];
+    if (opts && opts->raw_total)
+        for (size_t w = 0; w < 2 * (size_t)njobs; ++w) opts->raw_total[w] = res[w];
     return GP_OK;
 }
 
@@ -660,7 +679,8 @@ gp_status gp_count_batch_ranges(gp_graph* const* graphs, const gp_schedules* con
         r.split = (opts && opts->budget_cycles <= 0) ? opts->split : 0;   // whole ranges only
         gp_status rc = make_job(graphs[j], scheds[j], idx ? idx[j] : 0, &r, &jobs[j]);
         if (rc != GP_OK) return rc;
-        if (jobs[j].plan.iep) return fail(GP_ERR_ARG, "inclusion-exclusion plans count whole graphs only");
+        if (jobs[j].plan.iep && !(opts && opts->raw_total))
+            return fail(GP_ERR_ARG, "inclusion-exclusion jobs of a time slice need opts->raw_total");
         if (jobs[j].plan.labeled) return fail(GP_ERR_ARG, "labelled plans are counted by gp_count");
         if (graphs[j]->device != graphs[0]->device) return fail(GP_ERR_ARG, "graphs on different devices");
         jobs[j].task_offset = off;
@@ -677,11 +697,16 @@ gp_status gp_count_batch_ranges(gp_graph* const* graphs, const gp_schedules* con
                    &done, want_ms ? &ms : nullptr, nullptr, aborted.data());
     if (rc != GP_OK) return rc;
     for (int32_t j = 0; j < njobs; ++j)
-        if (res[2 * j + 1] && !aborted[j]) return fail(GP_ERR_OVERFLOW, "a count does not fit in 64 bits");
+        if (!jobs[j].plan.iep && res[2 * j + 1] && !aborted[j])
+            return fail(GP_ERR_OVERFLOW, "a count does not fit in 64 bits");
     bool all = true;
     for (int32_t j = 0; j < njobs; ++j) {
         int64_t p = std::min(std::max<int64_t>(done - jobs[j].task_offset, 0), jobs[j].ntasks);
-        out[j] = aborted[j] ? 0 : res[2 * j];
+        out[j] = (aborted[j] || jobs[j].plan.iep) ? 0 : res[2 * j];
+        if (opts && opts->raw_total) {
+            opts->raw_total[2 * j] = aborted[j] ? 0 : res[2 * j];
+            opts->raw_total[2 * j + 1] = aborted[j] ? 0 : res[2 * j + 1];
+        }
         next_task[j] = aborted[j] ? -1 : jobs[j].task_begin + p;
         all = all && !aborted[j] && p == jobs[j].ntasks;
     }
@@ -704,6 +729,15 @@ gp_status gp_schedule_set_iep(gp_schedules* s, int32_t enable, int32_t* n_iep) {
     }
     s->plans = plans;
     if (n_iep) *n_iep = n;
+    return GP_OK;
+}
+
+gp_status gp_schedule_iep(const gp_schedules* s, int32_t idx, int32_t* kk, uint32_t* divisor) {
+    if (!s) return fail(GP_ERR_ARG, "null schedule");
+    if (idx < 0 || idx >= (int32_t)s->plans.size()) return fail(GP_ERR_ARG, "plan index out of range");
+    const GpPlan& P = s->plans[idx];
+    if (kk) *kk = P.iep;
+    if (divisor) *divisor = P.iep ? P.iep_div : 1u;
     return GP_OK;
 }
 

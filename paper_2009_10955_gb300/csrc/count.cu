@@ -77,6 +77,10 @@ struct Acc {   // per-lane 128-bit counter
     unsigned long long lo = 0, hi = 0;
     __device__ __forceinline__ void add(unsigned long long x) { lo += x; hi += (lo < x); }
     __device__ __forceinline__ void sub(unsigned long long x) { hi -= (lo < x); lo -= x; }
+    __device__ __forceinline__ void add128(unsigned long long xl, unsigned long long xh) {
+        lo += xl;
+        hi += xh + (lo < xl);
+    }
 };
 
 __device__ void flush(Acc& acc, unsigned long long* res) {
@@ -114,10 +118,12 @@ struct TaskCtx {
     int lane_work;         // per-lane work limit before handing to the warp
     int* err;
     unsigned long long* sbytes;   // algorithmic-byte tally (instrumented kernel only)
+    unsigned long long* sops;     // bitmap word-operation tally (instrumented kernel only)
     const int32_t* labels; // vertex labels (labelled plans in the listing kernel)
     long long* deadline;   // this warp's current work-item deadline (shared memory; 0 = none)
     long long task_cycles; // work-item cycle limit (0 = none)
     int* job_abort;        // abort flag of the current job (global memory)
+    unsigned* iep_cnt;     // 32 counters per warp for inclusion-exclusion (shared memory)
 };
 
 // True (on every lane) once the current work item has outlived its cycle
@@ -220,12 +226,61 @@ __device__ __forceinline__ void tally(const TaskCtx& c, List a, List b, Window w
     }
 }
 
+// Lists whose lengths differ by at most this factor are intersected by the
+// tile merge below; longer ratios by binary search of the shorter list.
+constexpr int kMergeRatio = 4;
+
+// Tile merge of sorted lists A (na) and B (nb): each round loads 32 elements
+// of each (coalesced), every lane finds its A element among the 32 B
+// elements with a 5-step shuffle search, and the tile that ends first is
+// consumed. Invariant: B elements before ib are below A[ia], so an A element
+// not above the B tile's last element is matched exactly when it is in the
+// tile. Writes matches to out (in order) when out != nullptr.
+__device__ __forceinline__ int warp_merge(const TaskCtx& c, const int32_t* __restrict__ A, int na,
+                                          const int32_t* __restrict__ B, int nb,
+                                          int32_t* __restrict__ out, int cap, Acc* acc) {
+    const int lane = c.lane;
+    int ia = 0, ib = 0, total = 0;
+    while (ia < na && ib < nb) {
+        const int x = (ia + lane < na) ? __ldg(A + ia + lane) : INT_MAX;
+        const int y = (ib + lane < nb) ? __ldg(B + ib + lane) : INT_MAX;
+        const int amax = __shfl_sync(kFull, x, min(31, na - 1 - ia));
+        const int bmax = __shfl_sync(kFull, y, min(31, nb - 1 - ib));
+        int pos = 0;                                  // B elements of the tile below x
+#pragma unroll
+        for (int st = 16; st; st >>= 1)
+            if (__shfl_sync(kFull, y, pos + st - 1) < x) pos += st;
+        const bool mine = ia + lane < na && x <= bmax;   // resolved in this round
+        const bool f = mine && __shfl_sync(kFull, y, pos & 31) == x && pos < 32;
+        const unsigned m = __ballot_sync(kFull, f);
+        if (out && f) {
+            const int at = total + __popc(m & lanemask_lt());
+            if (at < cap) out[at] = x; else atomicExch(c.err, 2);
+        }
+        if (acc && f) acc->add(1);
+        total += __popc(m);
+        if (amax <= bmax) {                           // the A tile is resolved
+            ia += 32;
+            ib += __popc(__ballot_sync(kFull, ib + lane < nb && y <= amax));
+        } else {                                      // the B tile is used up
+            ia += __popc(__ballot_sync(kFull, mine));
+            ib += 32;
+        }
+    }
+    return total;
+}
+
 // Warp-cooperative intersection of a and b within window w. Writes the
 // (sorted) result to out when out != nullptr and returns its size
 // (warp-uniform). With acc != nullptr each lane also adds its own matches.
 __device__ __forceinline__ int warp_intersect(const TaskCtx& c, List a, List b, Window w,
                                               int32_t* __restrict__ out, int cap, Acc* acc) {
     const Probe q = choose(c, a, b, w);
+    if (!q.bitmap && q.it.n > 0 && q.pr.n <= kMergeRatio * q.it.n) {
+        const int total = warp_merge(c, q.it.p, q.it.n, q.pr.p, q.pr.n, out, cap, acc);
+        if (c.sbytes && c.lane == 0) tally(c, a, b, w, out ? 4ull * (unsigned long long)total : 0ull);
+        return total;
+    }
     const int n = q.it.n, lane = c.lane;
     int total = 0, from = q.bitmap ? q.tail : 0;
     for (int base = 0; base < n; base += 32) {
@@ -398,7 +453,7 @@ __device__ __forceinline__ bool count_last_lane(const TaskCtx& c, const int* v, 
 // S_b (depth k-1), minus already-matched vertices, and must differ:
 // |S_a| |S_b| - |S_a ∩ S_b|. The plan has no restriction acting at those
 // depths; the host divides the job's total by the plan's iep_div.
-__device__ __forceinline__ void iep_count(const TaskCtx& c, const int* v, Acc& acc) {
+__device__ __forceinline__ void iep_count2(const TaskCtx& c, const int* v, Acc& acc) {
     const GpPlan& P = *c.P;
     const int da = P.k - 2, db = P.k - 1;
     const GpLevel& LA = P.lvl[da];
@@ -417,6 +472,150 @@ __device__ __forceinline__ void iep_count(const TaskCtx& c, const int* v, Acc& a
         acc.add((unsigned long long)a * (unsigned long long)b);
         acc.sub((unsigned long long)(ab - both));
     }
+}
+
+// Is x in list a? Binary search from position `from` (x is not below a.p[from]
+// when from > 0); *pos receives the search position for the next, larger x.
+__device__ __forceinline__ bool member_from(const TaskCtx& c, List a, int x, int from, int* pos) {
+    if (is_core(c, a.v) && x < c.core_n) { *pos = from; return core_bit(c, a.v, x); }
+    const int p = from + lower_bound(a.p + from, a.n - from, x);
+    *pos = p;
+    return p < a.n && __ldg(a.p + p) == x;
+}
+
+// Inclusion-exclusion for the last kk >= 3 depths (Section IV-D). With the
+// outer depths 0 .. k-kk-1 bound, the inner vertices (pairwise non-adjacent,
+// no restriction among them or towards the outer ones) take values in
+// their candidate sets S_1 .. S_kk minus the matched outer vertices, and
+// must be pairwise distinct. The number of such tuples is
+//   sum over set partitions pi of {1..kk} of
+//       prod over blocks B of pi of (-1)^(|B|-1) (|B|-1)! |∩_{i in B} S_i|,
+// the terms of Algorithm 2's expansion grouped by the components they
+// produce. Every intersection size comes from one pass: each element x of
+// a set other than the largest gets the mask M(x) of the sets holding it
+// (counted once, at the first iterated set that holds it), the warp tallies
+// how many elements share each mask, and |∩_{i in T} S_i| is the sum of the
+// tallies of the masks containing T. Arithmetic is in 128 bits; the host
+// divides the job's total by the plan's iep_div.
+__device__ __noinline__ void iep_count_sets(const TaskCtx& c, const int* v, Acc& acc) {
+    const GpPlan& P = *c.P;
+    const int k = P.k, kk = P.iep, d0 = k - kk;
+    List S[GP_MAX_IEP];
+    int big = 0, big_n = -1;
+#pragma unroll
+    for (int i = 0; i < GP_MAX_IEP; ++i) {
+        S[i] = List{nullptr, 0, -1};
+        if (i < kk) {
+            const GpLevel& L = P.lvl[d0 + i];
+            S[i] = clip((L.src_kind == 1) ? nbr(c, v[L.src]) : slot(c, L.src), window(L.lo_mask, L.hi_mask, v));
+            if (S[i].n > big_n) { big = i; big_n = S[i].n; }
+        }
+    }
+    unsigned* cnt = c.iep_cnt;
+    cnt[c.lane] = 0u;
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < GP_MAX_IEP; ++i) {
+        if (i >= kk || i == big) continue;
+        int from[GP_MAX_IEP];
+#pragma unroll
+        for (int j = 0; j < GP_MAX_IEP; ++j) from[j] = 0;
+        const int n = S[i].n;
+        for (int base = 0; base < n; base += 32) {
+            const int idx = base + c.lane;
+            unsigned M = 0;
+            int pos[GP_MAX_IEP];
+#pragma unroll
+            for (int j = 0; j < GP_MAX_IEP; ++j) pos[j] = from[j];
+            if (idx < n) {
+                const int x = __ldg(S[i].p + idx);
+                bool dup = false;
+                M = 1u << i;
+#pragma unroll
+                for (int j = 0; j < GP_MAX_IEP; ++j) {
+                    if (j >= kk || j == i) continue;
+                    if (member_from(c, S[j], x, from[j], &pos[j])) {
+                        M |= 1u << j;
+                        dup |= (j < i && j != big);     // counted at an earlier set
+                    }
+                }
+                for (int j = 0; j < d0; ++j) dup |= (v[j] == x);   // a matched outer vertex
+                if (dup) M = 0;
+            }
+            const unsigned grp = __match_any_sync(kFull, M);
+            if (__popc(M) >= 2 && (__ffs(grp) - 1) == c.lane) cnt[M] += __popc(grp);
+            // later elements are larger: narrow the searches
+            const int last = min(31, n - 1 - base);
+#pragma unroll
+            for (int j = 0; j < GP_MAX_IEP; ++j) from[j] = __shfl_sync(kFull, pos[j], last);
+        }
+        if (c.sbytes && c.lane == 0)
+            for (int j = 0; j < kk; ++j)
+                if (j != i) *c.sbytes += intersect_bytes(n, S[j].n);
+    }
+    __syncwarp();
+    // superset sums: lane T holds |∩_{i in T} S_i| (without matched vertices)
+    unsigned long long val = cnt[c.lane];
+    for (int b = 0; b < kk; ++b) {
+        const unsigned long long o = __shfl_xor_sync(kFull, val, 1 << b);
+        if (!(c.lane >> b & 1)) val += o;
+    }
+    if (__popc(c.lane) == 1) {                  // single sets: |S_i| minus matched vertices
+        const int i = __ffs(c.lane) - 1;
+        if (i < kk) {
+            const GpLevel& L = P.lvl[d0 + i];
+            const Window w = window(L.lo_mask, L.hi_mask, v);
+            List si = S[0];
+#pragma unroll
+            for (int t = 1; t < GP_MAX_IEP; ++t) if (t == i) si = S[t];
+            val = (unsigned long long)(si.n - excluded_hits(c, L, d0, v, w, si, nullptr));
+        }
+    }
+    // every set partition of the kk sets as a restricted growth string
+    // g_0 .. g_{kk-1} (3 bits each): g_0 = 0 and g_i <= 1 + max(g_0 .. g_{i-1});
+    // block b holds the sets i with g_i = b. All lanes walk the same
+    // partitions, so every shuffle below is uniform.
+    __int128 total = 0;
+    unsigned g = 0;
+    for (;;) {
+        __int128 term = 1;
+        for (int blk = 0; blk < kk; ++blk) {
+            unsigned mask = 0;
+            for (int i = 0; i < kk; ++i)
+                if (((g >> (3 * i)) & 7u) == (unsigned)blk) mask |= 1u << i;
+            if (!mask) break;                     // blocks are numbered 0, 1, 2, ...
+            const long long card = (long long)__shfl_sync(kFull, val, (int)mask);
+            const int m = __popc(mask);
+            long long mu = 1;                     // (-1)^(m-1) (m-1)!
+            for (int t = 2; t < m; ++t) mu *= t;
+            if (!(m & 1)) mu = -mu;
+            term *= (__int128)(mu * card);
+        }
+        total += term;
+        int i = kk - 1;                           // next growth string
+        for (; i >= 1; --i) {
+            unsigned mx = 0;
+            for (int j = 0; j < i; ++j) mx = max(mx, (g >> (3 * j)) & 7u);
+            if (((g >> (3 * i)) & 7u) <= mx) {
+                g += 1u << (3 * i);
+                g &= (1u << (3 * (i + 1))) - 1u;  // zero the tail
+                break;
+            }
+        }
+        if (i < 1) break;
+    }
+    if (c.lane == 0) {
+        const unsigned __int128 r = (unsigned __int128)total;
+        acc.add128((unsigned long long)r, (unsigned long long)(r >> 64));
+    }
+}
+
+// kGeneralIep: the launch may hold plans with kk >= 3 (kernels launched
+// without such plans carry no call to iep_count_sets).
+template <bool kGeneralIep>
+__device__ __forceinline__ void iep_count(const TaskCtx& c, const int* v, Acc& acc) {
+    if (!kGeneralIep || c.P->iep == 2) iep_count2(c, v, acc);
+    else iep_count_sets(c, v, acc);
 }
 
 // The loop at depth k-2 with one candidate per lane: every lane counts the
@@ -494,7 +693,10 @@ __device__ __forceinline__ int bitmap_build(const TaskCtx& c, const int* v, int 
         const int Wi = min(Wd, Wprev);
         for (int w = c.lane; w < Wd; w += 32)
             S[w] = (w < Wi) ? (prev[w] & __ldg(row + w) & window_bits(w, win.lo, win.hi)) : 0u;
+        if (c.sops && c.lane == 0) *c.sops += (unsigned long long)Wi;          // one AND per word
     } else {
+        if (c.sops && c.lane == 0)                                             // operands - 1 ANDs per word
+            *c.sops += (unsigned long long)Wd * (unsigned)max(0, __popc(L.op_mask & ((1u << d) - 1u)) - 1);
         for (int w = c.lane; w < Wd; w += 32) {
             uint32_t x = window_bits(w, win.lo, win.hi);
             for (int j = 0; j < d && x; ++j)
@@ -552,6 +754,8 @@ __device__ __forceinline__ void bitmap_last_two(const TaskCtx& c, int* v, int W,
         }
         __syncwarp();
         PP = pp;
+        if (c.sops && c.lane == 0)
+            *c.sops += (unsigned long long)Wd * (unsigned)max(0, __popc(lv.op_mask & ((1u << d) - 1u)) - 1);
     }
     const bool any_excl = (lv.excl_mask & (uint8_t)((2u << d) - 1)) != 0;
     if (c.lane_bitmap) {
@@ -626,6 +830,7 @@ __device__ __forceinline__ void bitmap_last_two(const TaskCtx& c, int* v, int W,
                     }
                     cnt += __popc(m[0]) + __popc(m[1]) + __popc(m[2]) + __popc(m[3]);
                 }
+                if (c.sops) *c.sops += (unsigned long long)(w1 - w0) * (uses_x ? 2u : 1u);   // AND + POPC per word
             }
             if (any_excl) {
                 for (int jj = 0; jj <= d; ++jj) {
@@ -662,6 +867,7 @@ __device__ __forceinline__ void bitmap_last_two(const TaskCtx& c, int* v, int W,
             if (uses_x) m &= __ldg(rx + w);
             cnt += __popc(m);
         }
+        if (c.sops && c.lane == 0 && w1 > w0) *c.sops += (unsigned long long)(w1 - w0) * (uses_x ? 2u : 1u);
         acc.add(cnt);
         if (any_excl && c.lane == 0) {
             int hits = 0;
@@ -765,6 +971,7 @@ __device__ __forceinline__ void bitmap_last_three(const TaskCtx& c, int* v, int 
         const int hi_e = e_xhi ? min(be.hi, x) : be.hi;
         const int we0 = max(0, (lo_e + 1) >> 5);
         const int we1 = min(Ws, (hi_e == INT_MAX) ? Ws : ((hi_e + 31) >> 5));
+        if (c.sops && we1 > we0) *c.sops += (unsigned long long)(we1 - we0);   // S AND row(x) per word
         for (int w = we0; w < we1; ++w) {
             uint32_t m = S[w] & __ldg(rx + w);
             if (w == we0 || w == we1 - 1) m &= window_bits(w, lo_e, hi_e);
@@ -804,7 +1011,9 @@ __device__ __forceinline__ void bitmap_last_three(const TaskCtx& c, int* v, int 
                         }
                         cnt += __popc(t4[0]) + __popc(t4[1]) + __popc(t4[2]) + __popc(t4[3]);
                     }
+                    if (c.sops) *c.sops += 3ull * (unsigned long long)(w1 - w0);   // two ANDs + POPC per word
                 }
+                if (c.sops) *c.sops += 1;                                          // y taken from the set
                 if (ex_L) {
                     for (int jj = 0; jj < d; ++jj) {
                         if (!((ex_L >> jj) & 1)) continue;
@@ -835,6 +1044,7 @@ __device__ void bitmap_task(const TaskCtx& c, int* v, Acc& acc, int part, int np
             const int x = __ldg(a.p + i);
             atomicOr(c.bm + (x >> 5), 1u << (x & 31));
         }
+        if (c.sops && c.lane == 0) *c.sops += (unsigned long long)n;           // one OR per element
         __syncwarp();
     }
     if (k == 4) {
@@ -859,6 +1069,7 @@ __device__ void bitmap_task(const TaskCtx& c, int* v, Acc& acc, int part, int np
         if (over(c)) return;
         const int x = bitmap_next(c.bm + (size_t)d * c.bm_stride, Wd[d], word[d], bits[d]);
         if (x < 0) { --d; continue; }
+        if (c.sops && c.lane == 0) *c.sops += 1;                               // candidate taken from the set
         if (d == 2 && (ordinal2++ % nparts) != part) continue;  // another part's candidate
         v[d] = x;
         Wd[d + 1] = bitmap_build(c, v, d + 1, W, Wd[d], n0_smem);
@@ -876,6 +1087,7 @@ __device__ void bitmap_task(const TaskCtx& c, int* v, Acc& acc, int part, int np
 
 // Remaining loops of one edge task (v0, v1), or of part `part` of `nparts`
 // of it: the parts share out the candidates of depth 2.
+template <bool kGeneralIep>
 __device__ void run_task(const TaskCtx& c, int v0, int v1, Acc& acc, int part, int nparts) {
     const GpPlan& P = *c.P;
     const int k = P.k;
@@ -893,11 +1105,12 @@ __device__ void run_task(const TaskCtx& c, int v0, int v1, Acc& acc, int part, i
     v[0] = v0;
     v[1] = v1;
     if (P.core_dfs && c.bm && v1 < c.core_n) { bitmap_task(c, v, acc, part, nparts); return; }
-    if (k == 3 || (P.iep && k == 4)) {
+    const int d_iep = P.iep ? k - 1 - P.iep : -1;   // last outer depth of an inclusion-exclusion plan
+    if (k == 3 || d_iep == 1) {
         if (part != 0) return;                 // no depth-2 loop to share out
         run_builds(c, 1, v);
         if (k == 3) count_last(c, v, acc);
-        else iep_count(c, v, acc);
+        else iep_count<kGeneralIep>(c, v, acc);
         return;
     }
     run_builds(c, 1, v);
@@ -906,7 +1119,7 @@ __device__ void run_task(const TaskCtx& c, int v0, int v1, Acc& acc, int part, i
         lst[dd] = clip((L.src_kind == 1) ? nbr(c, v[L.src]) : slot(c, L.src), window(L.lo_mask, L.hi_mask, v));
         cur[dd] = 0;
     };
-    const bool lane_last = P.lvl[k - 2].nbuild == 0;
+    const bool lane_last = !P.iep && P.lvl[k - 2].nbuild == 0;
     int d = 2;
     prepare(2);
     if (nparts > 1) {                          // this part's share of depth 2
@@ -932,32 +1145,34 @@ __device__ void run_task(const TaskCtx& c, int v0, int v1, Acc& acc, int part, i
         if (skip) continue;
         v[d] = x;
         run_builds(c, d, v);
-        if (P.iep && d == k - 3) iep_count(c, v, acc);
+        if (d == d_iep) iep_count<kGeneralIep>(c, v, acc);
         else if (d == k - 2) count_last(c, v, acc);
         else { ++d; prepare(d); }
     }
 }
 
-template <bool kStats, int kMinBlocks>
+template <bool kStats, int kMinBlocks, bool kGeneralIep>
 __global__ void __launch_bounds__(kWarps * 32, kMinBlocks)
 k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
         unsigned long long* __restrict__ cursor, unsigned long long* __restrict__ results,
         int32_t* __restrict__ slot_pool, int64_t warp_elems, int chunk, long long budget,
         int* __restrict__ err, unsigned long long* __restrict__ stats, int lane_work, int use_core,
         int bm_stride, int bm_sets, long long task_cycles, int* __restrict__ aborts, int lane_bitmap) {
-    unsigned long long my_bytes = 0;
+    unsigned long long my_bytes = 0, my_ops = 0;
     extern __shared__ uint32_t s_bitmaps[];   // bm_sets x bm_stride words per warp (may be empty)
     __shared__ GpPlan s_plan[kWarps];
     __shared__ int s_len[kWarps][GP_MAX_SLOTS];
     __shared__ long long s_deadline[kWarps];
+    __shared__ unsigned s_iep[kWarps][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t gw = (int64_t)blockIdx.x * kWarps + w;
     TaskCtx c;
     c.P = &s_plan[w];
+    c.iep_cnt = s_iep[w];
     c.slots = slot_pool + gw * warp_elems;
     c.slen = s_len[w];
     c.bm_stride = bm_stride;
-    c.bm = (bm_stride > 0 && !kStats) ? s_bitmaps + (size_t)w * bm_sets * bm_stride : nullptr;
+    c.bm = (bm_stride > 0) ? s_bitmaps + (size_t)w * bm_sets * bm_stride : nullptr;
     c.lane = lane;
     c.lane_work = lane_work;
     c.deadline = &s_deadline[w];
@@ -978,6 +1193,7 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
     c.slot_cap = 0;
     c.n_vertices = 0;
     c.sbytes = kStats ? &my_bytes : nullptr;
+    c.sops = kStats ? &my_ops : nullptr;
     int cur_job = -1;
     int64_t job_lo = 0, job_hi = 0, job_begin = 0, job_heavy = 0;
     int job_split = 1;
@@ -1035,7 +1251,7 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
                 c.lane_bitmap = bitmap_mode != 0;
                 c.lane_three = bitmap_mode == 2;
                 if (c.core_n == 0 || J.core_words > c.bm_stride) c.bm = nullptr;
-                else if (bm_stride > 0 && !kStats && J.plan.k - 1 <= bm_sets)
+                else if (bm_stride > 0 && J.plan.k - 1 <= bm_sets)
                     c.bm = s_bitmaps + (size_t)w * bm_sets * bm_stride;
                 else c.bm = nullptr;
                 c.core_words = J.core_words;
@@ -1059,7 +1275,7 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
                 const int hv1 = __ldg(c.col + eh);
                 if (lo1s && !(hv1 > rl)) continue;
                 if (hi1s && !(hv1 < rl)) continue;
-                run_task(c, rl, hv1, acc, part, job_split);
+                run_task<kGeneralIep>(c, rl, hv1, acc, part, job_split);
             }
             if (lt >= lt_end) { t = tend; continue; }
             int64_t e = job_begin + job_heavy + (lt - hp);
@@ -1114,7 +1330,7 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
                     const int v1 = __ldg(c.col + e);
                     if (lo1 && !(v1 > v0)) continue;
                     if (hi1 && !(v1 < v0)) continue;
-                    run_task(c, v0, v1, acc, 0, 1);
+                    run_task<kGeneralIep>(c, v0, v1, acc, 0, 1);
                 }
             }
             t = tend;
@@ -1124,6 +1340,8 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
     if (kStats) {
         for (int o = 16; o; o >>= 1) my_bytes += __shfl_down_sync(kFull, my_bytes, o);
         if (lane == 0 && my_bytes) atomicAdd(stats, my_bytes);
+        for (int o = 16; o; o >>= 1) my_ops += __shfl_down_sync(kFull, my_ops, o);
+        if (lane == 0 && my_ops) atomicAdd(stats + 1, my_ops);
     }
 }
 
@@ -1193,6 +1411,7 @@ k_list(const CountJob* __restrict__ job, int64_t ntasks, unsigned long long* __r
     }
     TaskCtx c;
     c.P = &s_plan[w];
+    c.iep_cnt = nullptr;                        // listing plans never use inclusion-exclusion
     c.row_ptr = job->row_ptr;
     c.col = job->col;
     c.core_bits = job->core_bits;
@@ -1210,6 +1429,7 @@ k_list(const CountJob* __restrict__ job, int64_t ntasks, unsigned long long* __r
     c.lane_work = kLaneWork;
     c.err = err;
     c.sbytes = nullptr;
+    c.sops = nullptr;
     c.deadline = &s_deadline[w];
     c.task_cycles = 0;
     c.job_abort = err;
@@ -1330,20 +1550,28 @@ gp_status geometry(const CountJob* jobs, int njobs, const LaunchOpts& opt, Geome
     int want = opt.blocks_per_sm;
     if (want <= 0) {
         want = 4;
-        if (!opt.stats && !opt.no_core && opt.bitmap_mode == 2)
+        if (!opt.no_core && opt.bitmap_mode == 2)
             for (int j = 0; j < njobs; ++j) {
                 const GpPlan& P = jobs[j].plan;
                 if (P.core_dfs && jobs[j].core_bits && P.k >= 5 && P.lvl[P.k - 2].bm_inc && P.lvl[P.k - 1].bm_inc)
                     want = 3;
             }
     }
-    if (want == 1 || want == 2) g->kern = opt.stats ? k_count<true, 1> : k_count<false, 1>;
-    else if (want == 3) g->kern = opt.stats ? k_count<true, 3> : k_count<false, 3>;
-    else g->kern = opt.stats ? k_count<true, 4> : k_count<false, 4>;
+    bool general_iep = false;              // some job replaces three or more loops
+    for (int j = 0; j < njobs; ++j) general_iep |= jobs[j].plan.iep >= 3;
+    if (opt.stats) {
+        g->kern = (want == 1 || want == 2) ? k_count<true, 1, true>
+                : (want == 3) ? k_count<true, 3, true> : k_count<true, 4, true>;
+    } else if (general_iep) {
+        g->kern = k_count<false, 4, true>;
+    } else {
+        g->kern = (want == 1 || want == 2) ? k_count<false, 1, false>
+                : (want == 3) ? k_count<false, 3, false> : k_count<false, 4, false>;
+    }
     // bitmap sets in shared memory when some job may search a core subtree
     g->bm_stride = 0;
     g->bm_sets = 0;
-    if (!opt.stats && !opt.no_core)
+    if (!opt.no_core)
         for (int j = 0; j < njobs; ++j)
             if (jobs[j].plan.core_dfs && jobs[j].core_bits && jobs[j].core_n > 0) {
                 g->bm_stride = std::max(g->bm_stride, (int)jobs[j].core_words);
@@ -1379,7 +1607,7 @@ gp_status scratch_bytes(const CountJob* jobs, int njobs, const LaunchOpts& opt, 
 
 gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& opt, cudaStream_t st,
                     uint64_t* results, int64_t* processed, float* kernel_ms, uint64_t* algo_bytes,
-                    int* aborted) {
+                    int* aborted, uint64_t* algo_ops) {
     if (njobs <= 0) { set_error("no jobs"); return GP_ERR_ARG; }
     Geometry geo;
     gp_status grc = geometry(jobs, njobs, opt, &geo);
@@ -1395,8 +1623,9 @@ gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& opt, cuda
 
     // device buffers: job table, results (2 per job), cursor, error word
     const size_t jobs_b = sizeof(CountJob) * (size_t)njobs;
-    // results (2 per job), cursor, error word, stats, then one abort flag per job
-    const size_t res_b = sizeof(unsigned long long) * (2 * (size_t)njobs + 3) + sizeof(int) * (size_t)njobs;
+    // results (2 per job), cursor, error word, stats (bytes, operations), then
+    // one abort flag per job
+    const size_t res_b = sizeof(unsigned long long) * (2 * (size_t)njobs + 4) + sizeof(int) * (size_t)njobs;
     void* d_mem = nullptr;
     int32_t* d_slots = nullptr;
     GP_CUDA_TRY(cudaMallocAsync(&d_mem, jobs_b + res_b + 64, st));
@@ -1411,7 +1640,7 @@ gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& opt, cuda
     unsigned long long* d_cursor = d_res + 2 * njobs;
     int* d_err = reinterpret_cast<int*>(d_cursor + 1);
     unsigned long long* d_stats = d_cursor + 2;
-    int* d_aborts = reinterpret_cast<int*>(d_stats + 1);
+    int* d_aborts = reinterpret_cast<int*>(d_stats + 2);
     gp_status rc = GP_OK;
     std::vector<unsigned long long> h_res((res_b + 7) / 8, 0);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -1454,8 +1683,9 @@ gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& opt, cuda
     }
     for (int j = 0; j < 2 * njobs; ++j) results[j] = h_res[j];
     if (algo_bytes) *algo_bytes = h_res[2 * njobs + 2];
+    if (algo_ops) *algo_ops = h_res[2 * njobs + 3];
     if (aborted) {
-        const int* flags = reinterpret_cast<const int*>(h_res.data() + 2 * njobs + 3);
+        const int* flags = reinterpret_cast<const int*>(h_res.data() + 2 * njobs + 4);
         for (int j = 0; j < njobs; ++j) aborted[j] = flags[j];
     }
     int64_t done = (int64_t)std::min<unsigned long long>(h_res[2 * njobs], (unsigned long long)total);
@@ -1468,7 +1698,7 @@ gp_status run_count_in_scratch(const CountJob* jobs, int njobs, void* d_scratch,
     constexpr int kMaxJobs = 8;            // host result words live on the stack
     if (njobs <= 0 || njobs > kMaxJobs) { set_error("1 to %d jobs per call", kMaxJobs); return GP_ERR_ARG; }
     // layout: [result words | job table | intermediate sets], 256-byte aligned
-    const size_t words_b = ((sizeof(unsigned long long) * (2 * (size_t)njobs + 4)) + 255) & ~(size_t)255;
+    const size_t words_b = ((sizeof(unsigned long long) * (2 * (size_t)njobs + 5)) + 255) & ~(size_t)255;
     const size_t jobs_b = ((sizeof(CountJob) * (size_t)njobs) + 255) & ~(size_t)255;
     if (words_b + jobs_b > scratch_bytes) {
         set_error("%d jobs need %zu bytes of fixed scratch for results and job table; it holds %zu",
@@ -1490,7 +1720,9 @@ gp_status run_count_in_scratch(const CountJob* jobs, int njobs, void* d_scratch,
     int dev = 0, nsm = 0, occ = 0;
     GP_CUDA_TRY(cudaGetDevice(&dev));
     GP_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    auto kern = k_count<false, 4>;
+    bool general_iep = false;
+    for (int j = 0; j < njobs; ++j) general_iep |= jobs[j].plan.iep >= 3;
+    auto kern = general_iep ? k_count<false, 4, true> : k_count<false, 4, false>;
     GP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWarps * 32, 0));
     int64_t blocks = std::min<int64_t>((int64_t)nsm * std::max(occ, 1), (int64_t)(slot_b / per_block));
     int64_t per_warp = total / (blocks * kWarps * 64);
@@ -1500,7 +1732,7 @@ gp_status run_count_in_scratch(const CountJob* jobs, int njobs, void* d_scratch,
     unsigned long long* d_cursor = d_res + 2 * njobs;
     int* d_err = reinterpret_cast<int*>(d_cursor + 1);
     unsigned long long* d_stats = d_cursor + 2;
-    int* d_aborts = reinterpret_cast<int*>(d_stats + 1);       // unused: no cycle limit here
+    int* d_aborts = reinterpret_cast<int*>(d_stats + 2);       // unused: no cycle limit here
     CountJob* d_jobs = reinterpret_cast<CountJob*>(base + words_b);
     int32_t* d_slots = reinterpret_cast<int32_t*>(base + words_b + jobs_b);
     unsigned long long h_res[2 * kMaxJobs + 3] = {};

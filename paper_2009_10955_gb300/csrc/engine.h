@@ -84,7 +84,7 @@ struct LaunchOpts {
     int blocks_per_sm = 0;   // 0 = occupancy maximum
     int chunk = 0;           // 0 = automatic
     int64_t budget_cycles = 0;
-    bool stats = false;      // instrumented kernel that tallies algorithmic bytes
+    bool stats = false;      // instrumented kernel that tallies algorithmic bytes and operations
     bool no_core = false;    // binary searches only (no core bit matrix)
     int64_t task_cycles = 0; // per-work-item cycle limit (0 = none)
     int bitmap_mode = 2;     // bitmap subtree: 0 warp per candidate, 1 lane per candidate (last two levels), 2 (default) also the lane three-level tail
@@ -94,9 +94,11 @@ struct LaunchOpts {
 // Run the jobs in one persistent launch. results[2 j], results[2 j + 1]
 // receive job j's 128-bit count (lo, hi). *processed receives how many
 // global tasks (from 0) were completed (< total only with a budget).
+// With lo.stats, *algo_bytes receives the list-path bytes and *algo_ops the
+// bitmap-subtree word operations of the launch.
 gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& lo, cudaStream_t st,
                     uint64_t* results, int64_t* processed, float* kernel_ms = nullptr,
-                    uint64_t* algo_bytes = nullptr, int* aborted = nullptr);
+                    uint64_t* algo_bytes = nullptr, int* aborted = nullptr, uint64_t* algo_ops = nullptr);
 
 // run_count without allocating: results, job table and intermediate sets all
 // live in the caller's device buffer d_scratch (256-byte aligned); the grid

@@ -14,6 +14,7 @@
 #define GP_MAX_K 7
 #define GP_MAX_SLOTS 16
 #define GP_MAX_BUILDS 8
+#define GP_MAX_IEP 5     // most innermost loops that inclusion-exclusion replaces
 
 // One incremental intersection: slot[dst] = base ∩ N(v_d), clipped to the
 // window of the consuming depth that is already known at depth d.
@@ -50,10 +51,13 @@ struct GpPlan {
     int16_t last_base;
     int8_t order[GP_MAX_K];   // pattern vertex searched at depth d
     int8_t pad[1];
-    // Inclusion-exclusion counting of the last two (non-adjacent) depths
-    // (Section IV-D with k = 2): at depth k-3 the contribution is
-    // |S_{k-2}| |S_{k-1}| - |S_{k-2} ∩ S_{k-1}|; restrictions acting at the
-    // last two depths are dropped, and the job's total is divided by iep_div.
+    // Inclusion-exclusion counting of the last iep (= kk >= 2, 0: off)
+    // depths, whose vertices are pairwise non-adjacent (Section IV-D): once
+    // the outer depths 0 .. k-kk-1 are bound, the number of ways to pick kk
+    // distinct vertices from the inner candidate sets is added, expanded
+    // over the set partitions of the kk sets (Algorithm 2 gives each term's
+    // intersection). Restrictions acting at inner depths are dropped, and
+    // the job's total is divided by iep_div.
     int32_t iep;
     uint32_t iep_div;
     // 1 when every vertex searched after depth 1 is restricted below v_1:

@@ -425,15 +425,18 @@ bool compile_plan(const PatternInfo& p, const int8_t* sched, ResMask res, GpPlan
     return true;
 }
 
-bool iep_divisor(const PatternInfo& p, const int8_t* sched, ResMask res, ResMask* outer, uint32_t* div) {
+bool iep_divisor(const PatternInfo& p, const int8_t* sched, ResMask res, int kk, ResMask* outer, uint32_t* div) {
     const int k = p.k;
-    if (k < 4 || p.adj[sched[k - 1]][sched[k - 2]]) return false;
+    if (p.labeled || kk < 2 || kk > GP_MAX_IEP || k - kk < 2) return false;
+    for (int a = k - kk; a < k; ++a)
+        for (int b = a + 1; b < k; ++b)
+            if (p.adj[sched[a]][sched[b]]) return false;
     int pos[GP_MAX_K];
     for (int i = 0; i < k; ++i) pos[sched[i]] = i;
     ResMask ro = 0;
     for (ResMask m = res; m; m &= m - 1) {
         const int bit = __builtin_ctzll(m);
-        if (std::max(pos[bit / GP_MAX_K], pos[bit % GP_MAX_K]) <= k - 3) ro |= 1ull << bit;
+        if (std::max(pos[bit / GP_MAX_K], pos[bit % GP_MAX_K]) < k - kk) ro |= 1ull << bit;
     }
     const OrderTable& t = order_table(k);
     long mult = -1;
@@ -457,22 +460,39 @@ bool iep_divisor(const PatternInfo& p, const int8_t* sched, ResMask res, ResMask
     return true;
 }
 
+int iep_depth(const PatternInfo& p, const int8_t* sched) {
+    const int k = p.k;
+    int kk = 1;                                 // trailing vertices pairwise non-adjacent
+    while (kk < k) {
+        const int a = k - 1 - kk;
+        bool free = true;
+        for (int b = a + 1; b < k && free; ++b) free = !p.adj[sched[a]][sched[b]];
+        if (!free) break;
+        ++kk;
+    }
+    return std::min(kk, std::min(k - 2, GP_MAX_IEP));
+}
+
 bool compile_plan_iep(const PatternInfo& p, const int8_t* sched, ResMask res, GpPlan* out,
                       std::string& err) {
-    ResMask ro = 0;
-    uint32_t div = 0;
-    if (!iep_divisor(p, sched, res, &ro, &div)) {
-        err = "inclusion-exclusion does not apply to this configuration";
-        return false;
+    // the largest kk whose multiplicity is the same for every relative order
+    for (int kk = iep_depth(p, sched); kk >= 2; --kk) {
+        ResMask ro = 0;
+        uint32_t div = 0;
+        if (!iep_divisor(p, sched, res, kk, &ro, &div)) continue;
+        if (!compile_plan(p, sched, ro, out, err)) return false;
+        const int k = p.k;
+        out->iep = kk;
+        out->iep_div = div;
+        out->core_dfs = 0;
+        // the inner vertices are never bound: only outer ones can be matched
+        // vertices inside an inner candidate set
+        const uint8_t outer_mask = (uint8_t)((1u << (k - kk)) - 1u);
+        for (int x = k - kk; x < k; ++x) out->lvl[x].excl_mask &= outer_mask;
+        return true;
     }
-    if (!compile_plan(p, sched, ro, out, err)) return false;
-    const int k = p.k;
-    out->iep = 1;
-    out->iep_div = div;
-    out->core_dfs = 0;
-    // depth k-2 is not bound when the last set is counted
-    out->lvl[k - 1].excl_mask &= (uint8_t)~(1u << (k - 2));
-    return true;
+    err = "inclusion-exclusion does not apply to this configuration";
+    return false;
 }
 
 std::vector<Config> rank_configs(PatternInfo& p, double n_vertices, double n_edges,

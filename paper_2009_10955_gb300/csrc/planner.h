@@ -65,16 +65,24 @@ int upper_bound_restrictions(const int8_t* sched, ResMask res, int k);
 bool compile_plan(const PatternInfo& p, const int8_t* sched, ResMask res, GpPlan* out,
                   std::string& err);
 
-// Inclusion-exclusion over the last two depths (Section IV-D, k = 2):
-// applicable when k >= 4 and the last two searched vertices are not adjacent.
-// The restrictions whose later endpoint is one of them are dropped; every
-// embedding is then found once per automorphism sigma whose relabelled map
-// still obeys the remaining ("outer") restrictions. Dividing by that number
-// is exact only if it is the same for all k! relative orders of the
-// vertices; *div receives it and the call returns false when it varies.
-bool iep_divisor(const PatternInfo& p, const int8_t* sched, ResMask res, ResMask* outer, uint32_t* div);
+// Inclusion-exclusion over the last kk depths (Section IV-D): applicable
+// when the last kk searched vertices are pairwise non-adjacent, 2 <= kk <=
+// GP_MAX_IEP and at least two vertices stay outside (the edge task binds
+// them). The restrictions whose later endpoint is one of the kk inner
+// vertices are dropped; every embedding is then found once per automorphism
+// sigma whose relabelled map still obeys the remaining ("outer")
+// restrictions. Dividing by that number is exact only if it is the same for
+// all k! relative orders of the vertices; *div receives it and the call
+// returns false when it varies.
+bool iep_divisor(const PatternInfo& p, const int8_t* sched, ResMask res, int kk, ResMask* outer, uint32_t* div);
 
-// compile_plan for the inclusion-exclusion form (false when not applicable).
+// Number of trailing vertices of the schedule that are pairwise
+// non-adjacent, capped at min(k - 2, GP_MAX_IEP): the largest kk that
+// inclusion-exclusion could replace.
+int iep_depth(const PatternInfo& p, const int8_t* sched);
+
+// compile_plan for the inclusion-exclusion form with the largest kk that has
+// an exact divisor (false when none applies).
 bool compile_plan_iep(const PatternInfo& p, const int8_t* sched, ResMask res, GpPlan* out,
                       std::string& err);
 

@@ -18,6 +18,16 @@ halves below what the job managed when the slice ended first (leaving the
 rest of the next slice to the others); and the job order rotates from slice
 to slice, so that every job is at the front in turn.
 
+Plans use inclusion-exclusion for their innermost loops where it applies
+(Section IV-D); a slice then returns each job's undivided 128-bit partial
+total, the partial totals add up over the slices, and the request's count is
+their sum divided by the plan's divisor.
+
+Planning (and sizing a request's scratch) runs in the server thread without
+holding the lock that submit() takes, so clients are never blocked behind the
+planner, and a request's latency runs from the arrival time stamped before
+submit() takes that lock (or given by the caller).
+
 The scheduling here is host-side bookkeeping; all counting runs in the
 library's kernels.
 """
@@ -45,7 +55,7 @@ def next_quota(quota, done, finished_window, quota_min):
 
 class Request:
     __slots__ = ("rid", "graph", "adj", "arrival", "done", "count", "error", "finish", "sched",
-                 "next_task", "end_task", "acc", "slices", "scratch", "quota")
+                 "next_task", "end_task", "acc", "slices", "scratch", "quota", "div")
 
     def __init__(self, rid, graph, adj, arrival):
         self.rid = rid
@@ -63,6 +73,7 @@ class Request:
         self.slices = 0
         self.scratch = 0
         self.quota = 0
+        self.div = 1
 
     @property
     def latency(self):
@@ -74,7 +85,7 @@ class Server:
 
     def __init__(self, graphs, slice_ms=20.0, max_batch=256, mem_budget=None, stream=None,
                  clock_ghz=1.9, max_slices=None, item_ms=None, deadline_s=None, quota0=4096,
-                 quota_min=64):
+                 quota_min=64, iep=True):
         self.graphs = dict(graphs)
         self.slice_cycles = int(slice_ms * 1e-3 * clock_ghz * 1e9)
         # with item_ms, a single work item (edge task) that needs longer than
@@ -88,6 +99,7 @@ class Server:
         self.deadline_s = deadline_s      # wall-clock limit per request (from arrival)
         self.quota0 = quota0              # first task window of a job (tasks per slice)
         self.quota_min = quota_min
+        self.iep = iep                    # inclusion-exclusion where a plan qualifies
         self._plans = {}
         self._pending = collections.deque()
         self._active = []
@@ -101,9 +113,12 @@ class Server:
 
     # ------------------------------------------------------------ client side
     def submit(self, graph, adj, arrival=None):
+        """Queue a request. Its latency runs from `arrival` (perf_counter
+        seconds), stamped here before any lock is taken when not given."""
+        t = time.perf_counter() if arrival is None else arrival
         with self._cv:
             self._rid += 1
-            r = Request(self._rid, graph, adj, time.perf_counter() if arrival is None else arrival)
+            r = Request(self._rid, graph, adj, t)
             self._pending.append(r)
             self._cv.notify()
         return r
@@ -121,30 +136,42 @@ class Server:
         if s is None:
             g = self.graphs[graph]
             s = N.gp_schedule(N.gp_pattern_create(adj), g, top_k=1, stream=self.stream)
+            if self.iep:
+                s.set_iep(True)
             self._plans[key] = s
         return s
 
     def _admit(self):
         """Move pending requests into the active set while the batch's
-        scratch (the maximum over its jobs) fits the memory budget."""
-        while self._pending and len(self._active) < self.max_batch:
-            r = self._pending[0]
+        scratch (the maximum over its jobs) fits the memory budget. The
+        candidates are taken under the lock, planned and sized without it,
+        and admitted (in arrival order) under it again."""
+        with self._cv:
+            room = self.max_batch - len(self._active)
+            cand = [self._pending.popleft() for _ in range(min(room, len(self._pending)))]
+        planned = []
+        for r in cand:
             try:
                 r.sched = self._plan(r.graph, r.adj)
                 r.scratch = N.gp_count_scratch_bytes(self.graphs[r.graph], r.sched, 0)
+                r.div = r.sched.iep(0)[1]
             except Exception as e:  # bad pattern or graph: answer with the error
-                self._pending.popleft()
                 r.error = e
                 r.finish = time.perf_counter()
                 r.done.set()
                 continue
-            need = max([a.scratch for a in self._active] + [r.scratch])
-            if self.mem_budget is not None and self._active and need > self.mem_budget:
-                break
-            self._pending.popleft()
-            r.next_task, r.end_task = 0, self._nnz[r.graph]
-            r.quota = self.quota0
-            self._active.append(r)
+            planned.append(r)
+        with self._cv:
+            back = []
+            for r in planned:
+                need = max([a.scratch for a in self._active] + [r.scratch])
+                if back or (self.mem_budget is not None and self._active and need > self.mem_budget):
+                    back.append(r)              # waits, and so does every later request
+                    continue
+                r.next_task, r.end_task = 0, self._nnz[r.graph]
+                r.quota = self.quota0
+                self._active.append(r)
+            self._pending.extendleft(reversed(back))
 
     def _loop(self):
         while True:
@@ -153,7 +180,8 @@ class Server:
                     self._cv.wait()
                 if self._stop and not self._pending and not self._active:
                     return
-                self._admit()
+            self._admit()
+            with self._cv:
                 batch = list(self._active)
             if not batch:
                 continue
@@ -161,11 +189,12 @@ class Server:
             batch = batch[rot:] + batch[:rot]
             window = [min(r.end_task, r.next_task + r.quota) for r in batch]
             opts = N.make_opts(budget_cycles=self.slice_cycles, task_cycles=self.item_cycles)
+            raw = np.zeros(2 * len(batch), dtype=np.uint64)
             try:
                 st, out, nxt = N.gp_count_batch_ranges(
                     [self.graphs[r.graph] for r in batch], [r.sched for r in batch],
                     [0] * len(batch), [r.next_task for r in batch], window,
-                    opts, stream=self.stream)
+                    opts, stream=self.stream, raw=raw)
             except Exception as e:
                 now = time.perf_counter()
                 with self._cv:
@@ -178,18 +207,23 @@ class Server:
             now = time.perf_counter()
             with self._cv:
                 still = []
-                for r, c, t, w in zip(batch, out, nxt, window):
+                for j, (r, t, w) in enumerate(zip(batch, nxt, window)):
                     r.slices += 1
                     if int(t) < 0:                       # a work item outlived item_cycles
                         r.error = TimeoutError(f"request {r.rid}: a work item exceeded the item limit")
                         r.finish = now
                         r.done.set()
                         continue
-                    r.acc += int(c)
+                    r.acc += int(raw[2 * j]) | (int(raw[2 * j + 1]) << 64)
                     r.quota = next_quota(r.quota, int(t) - r.next_task, int(t) >= w, self.quota_min)
                     r.next_task = int(t)
                     if r.next_task >= r.end_task:
-                        r.count, r.finish = r.acc, now
+                        if r.acc % r.div or (r.acc // r.div) >> 64:
+                            r.error = ArithmeticError(f"request {r.rid}: total {r.acc} is not a 64-bit "
+                                                      f"multiple of its divisor {r.div}")
+                        else:
+                            r.count = r.acc // r.div
+                        r.finish = now
                         r.done.set()
                     elif self.max_slices is not None and r.slices >= self.max_slices:
                         r.error = TimeoutError(f"request {r.rid} exceeded {self.max_slices} slices")

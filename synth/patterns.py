@@ -8,7 +8,10 @@ Named patterns follow the workloads the counts are quoted on:
 * ``k6e``: the 6-clique minus the edge 0-1;
 * ``c6chord``: the 6-cycle plus the chord 0-2 (a triangle and a 5-cycle);
 * ``grid3x2``: the 3 x 2 grid 0-1-2 / 3-4-5 with rungs 0-3, 1-4, 2-5;
-* ``path3`` .. ``path5``, ``star4``, ``diamond``, ``tailed_triangle``.
+* ``path3`` .. ``path5``, ``star4``, ``diamond``, ``tailed_triangle``;
+* ``star5`` .. ``star7``: a centre 0 with 4 .. 6 leaves;
+* ``three_ears``: the triangle 0-1-2 with vertex 3 on edge 0-1, 4 on 1-2
+  and 5 on 0-2 (three pairwise non-adjacent vertices last).
 """
 
 import numpy as np
@@ -51,6 +54,10 @@ NAMED_PATTERNS = {
     "star4": (4, [(0, 1), (0, 2), (0, 3)]),
     "diamond": (4, [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3)]),
     "tailed_triangle": (4, [(0, 1), (1, 2), (2, 0), (2, 3)]),
+    "star5": (5, [(0, i) for i in range(1, 5)]),
+    "star6": (6, [(0, i) for i in range(1, 6)]),
+    "star7": (7, [(0, i) for i in range(1, 7)]),
+    "three_ears": (6, [(0, 1), (1, 2), (0, 2), (3, 0), (3, 1), (4, 1), (4, 2), (5, 0), (5, 2)]),
 }
 
 

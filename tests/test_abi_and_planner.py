@@ -156,6 +156,40 @@ def test_iep_switch_on_plans_that_do_not_qualify(N):
     assert lib.gp_schedule_set_iep(house.h, 0, ctypes.byref(n_iep)) == N.GP_OK
 
 
+def _iep_form(adj, order, res):
+    """The innermost-loop count kk and divisor that the definitions of
+    Section IV-D give for one configuration: the largest kk <= min(k - 2, 5)
+    whose last kk vertices are pairwise non-adjacent and for which the
+    number of automorphic copies obeying the outer restrictions is the same
+    for every relative order of the k vertices."""
+    from itertools import permutations
+    k = len(adj)
+    auts = pr.automorphisms(adj)
+    pos = {v: i for i, v in enumerate(order)}
+    for kk in range(min(k - 2, 5), 1, -1):
+        inner = order[k - kk:]
+        if any(adj[a][b] for a in inner for b in inner if a != b):
+            continue
+        ro = [(a, b) for a, b in res if max(pos[a], pos[b]) < k - kk]
+        m = {sum(1 for sg in auts if all(pi[sg[a]] > pi[sg[b]] for a, b in ro)) for pi in permutations(range(k))}
+        if len(m) == 1 and next(iter(m)) > 0:
+            return kk, next(iter(m))
+    return 0, 1
+
+
+@pytest.mark.parametrize("name", ["house", "k6e", "c6chord", "grid3x2", "star4", "star5", "star6", "star7",
+                                  "three_ears", "path5", "k4"])
+def test_iep_form_of_top_plans(N, name):
+    adj = named_pattern(name)
+    sc = N.gp_schedule(N.gp_pattern_create(adj), None, top_k=4)
+    sc.set_iep(True)
+    for i in range(len(sc)):
+        order, res, _ = sc.get(i)
+        assert sc.iep(i) == _iep_form(adj.tolist(), list(order), list(res)), (name, i, order, res)
+    sc.set_iep(False)
+    assert all(sc.iep(i) == (0, 1) for i in range(len(sc)))
+
+
 def test_labeled_pattern_groups(N):
     # equal labels give the plain group; alternating labels keep the
     # rotations by two and the reflections that fix the label classes;

@@ -363,3 +363,107 @@ def test_chung_lu_4m_sampled_roots(N):
         st, c = N.gp_count(g, s, 0, o)
         expect = oracle.count_restricted(adj, order, res, ref, root_begin=r, root_end=r + 1)
         assert c == expect, (r, int(deg[r]))
+
+
+# ----------------------------------------------- full-size hub roots, whole counts
+
+ORACLE_LEAVES_PER_WINDOW = 300_000_000     # keeps each oracle call within seconds
+
+
+def _hub_windows(N, g, s, ref, roots, width=64):
+    """CSR entry windows inside the rows of high-degree roots (their first,
+    middle and last `width` entries), each narrowed from its start until the
+    GPU count of the window is small enough for the oracle's enumeration,
+    which visits every embedding one by one."""
+    out = []
+    for r in roots:
+        b, e = int(ref.row_ptr[r]), int(ref.row_ptr[r + 1])
+        for a in sorted({b, max(b, (b + e) // 2 - width // 2), max(b, e - width)}):
+            z = min(e, a + width)
+            while z > a:
+                c = N.gp_count(g, s, 0, N.make_opts(task_begin=a, task_end=z))[1]
+                if c <= ORACLE_LEAVES_PER_WINDOW:
+                    out.append((r, a, z, c))
+                    break
+                z = a + (z - a) // 2
+    return out
+
+
+def _hub_roots(ref, extra, seed):
+    deg = np.diff(ref.row_ptr)
+    big = np.nonzero(deg > 2000)[0]
+    rng = np.random.default_rng(seed)
+    pick = [0, 1, 2] + sorted(rng.choice(big[3:], size=min(extra, max(0, len(big) - 3)), replace=False).tolist())
+    return pick, deg
+
+
+@pytest.mark.parametrize("pname", ["triangle", "k4", "house", "k5", "diamond"])
+def test_rmat20_hub_roots(N, pname):
+    """Full-size R-MAT scale 20, roots of degree > 2000 (the three highest
+    and two sampled): windows of their edge tasks, counted whole and with
+    every task cut into 8 parts (the split heavy prefix), equal the oracle's
+    restricted enumeration of the same CSR entries with the same plan."""
+    g, ref = graph_pair(N, "rmat20")
+    adj = named_pattern(pname)
+    s = N.gp_schedule(N.gp_pattern_create(adj), g)
+    order, res, _ = s.get(0)
+    roots, deg = _hub_roots(ref, 2, seed=7)
+    wins = _hub_windows(N, g, s, ref, roots)
+    assert len({r for r, *_ in wins}) >= 4, wins
+    for r, a, z, c in wins:
+        assert deg[r] > 2000
+        expect = oracle.count_restricted_entries(adj, order, res, ref, a, z)
+        assert c == expect, (pname, r, a, z)
+        for split in (8,):
+            assert N.gp_count(g, s, 0, N.make_opts(task_begin=a, task_end=z, split=split)) == (N.GP_OK, expect)
+
+
+def test_chung_lu_4m_hub_roots(N):
+    """Full-size Chung-Lu workload: K6-e over windows of the edge tasks of
+    roots of degree > 2000, whole and split, against the oracle."""
+    g, ref = graph_pair(N, "cl4m")
+    adj = named_pattern("k6e")
+    s = N.gp_schedule(N.gp_pattern_create(adj), g)
+    order, res, _ = s.get(0)
+    roots, deg = _hub_roots(ref, 2, seed=8)
+    wins = _hub_windows(N, g, s, ref, roots)
+    assert len({r for r, *_ in wins}) >= 4, wins
+    for r, a, z, c in wins:
+        assert deg[r] > 2000
+        expect = oracle.count_restricted_entries(adj, order, res, ref, a, z)
+        assert c == expect, (r, a, z)
+        assert N.gp_count(g, s, 0, N.make_opts(task_begin=a, task_end=z, split=8)) == (N.GP_OK, expect)
+
+
+@pytest.mark.parametrize("pname", ["triangle", "k4", "k5"])
+def test_rmat20_whole_counts_agree_across_plans_and_paths(N, pname):
+    """Full-size whole counts the oracle cannot finish: the three plans the
+    model ranks first, the list path alone (no core bit matrix), the three
+    bitmap-subtree variants and split heavy tasks all give one count."""
+    g, _ = graph_pair(N, "rmat20")
+    s = N.gp_schedule(N.gp_pattern_create(named_pattern(pname)), g, top_k=3)
+    base = N.gp_count(g, s, 0)
+    assert base[0] == N.GP_OK and base[1] > 0
+    for i in range(1, len(s)):
+        assert N.gp_count(g, s, i) == base, i
+    for f in (N.GP_COUNT_NO_CORE, N.GP_COUNT_WARP_BITMAP, N.GP_COUNT_LANE_BITMAP):
+        assert N.gp_count(g, s, 0, N.make_opts(flags=f)) == base, f
+    assert N.gp_count(g, s, 0, N.make_opts(split=8)) == base
+
+
+def test_chung_lu_4m_whole_k6e_agrees_across_plans_and_paths(N):
+    """Full-size K6-e on the Chung-Lu workload: the top three plans, the
+    list path without the core bit matrix, inclusion-exclusion over the
+    last two loops and split heavy tasks give one count."""
+    g, _ = graph_pair(N, "cl4m")
+    adj = named_pattern("k6e")
+    s = N.gp_schedule(N.gp_pattern_create(adj), g, top_k=3)
+    base = N.gp_count(g, s, 0)
+    assert base[0] == N.GP_OK and base[1] > 0
+    for i in range(1, len(s)):
+        assert N.gp_count(g, s, i) == base, i
+    assert N.gp_count(g, s, 0, N.make_opts(flags=N.GP_COUNT_NO_CORE)) == base
+    assert N.gp_count(g, s, 0, N.make_opts(split=8)) == base
+    si = N.gp_schedule(N.gp_pattern_create(adj), g)
+    assert si.set_iep(True) == 1
+    assert N.gp_count(g, si, 0) == base

@@ -22,10 +22,10 @@ SRC = os.path.join(os.path.dirname(os.path.abspath(oracle.__file__)), "oracle.c"
 MUTANTS = [
     ("keeps_self_loops", "if (u == v) continue;", ";"),
     ("keeps_duplicates", "if (i == 0 || key[i] != key[i - 1]) key[out++] = key[i];", "key[out++] = key[i];"),
-    ("not_injective", "for (int j = 0; j < d && ok; ++j) if (img[j] == v) ok = 0;          /* injective */", ";"),
-    ("drops_an_edge_check", "if (!has_edge(w, img[w->chk[d][c]], v)) ok = 0;                  /* edges */",
-     "if (c > 0 && !has_edge(w, img[w->chk[d][c]], v)) ok = 0;"),
-    ("ignores_restrictions", "if (w->res_gt[d][r] ? !(v > o) : !(v < o)) ok = 0;               /* restriction */",
+    ("not_injective", "for (int j = 0; j < d; ++j) if (img[j] == v) return 0;                 /* injective */", ";"),
+    ("drops_an_edge_check", "if (!has_edge(w, img[w->chk[d][c]], v)) return 0;                   /* edges */",
+     "if (c > 0 && !has_edge(w, img[w->chk[d][c]], v)) return 0;"),
+    ("ignores_restrictions", "if (w->res_gt[d][r] ? !(v > o) : !(v < o)) return 0;                /* restriction */",
      ";"),
     ("misses_last_neighbour", "    return lo < w->row_ptr[u + 1] && w->col[lo] == v;",
      "    return lo < w->row_ptr[u + 1] - 1 && w->col[lo] == v;"),
@@ -34,10 +34,15 @@ MUTANTS = [
     ("wrong_divisor", "    if (maps % aut) return -3;\n    u128 q = maps / aut;",
      "    u128 q = maps / (aut > 1 ? aut / 2 : aut);"),
     ("triangles_counted_twice", "                    if (c <= b) continue;\n", ""),
-    ("ignores_graph_labels", "if (ok && w->glab && w->glab[v] != w->plab[d]) ok = 0;", ";"),
+    ("ignores_graph_labels", "if (w->glab && w->glab[v] != w->plab[d]) return 0;                     /* label */", ";"),
     ("ignores_the_root_label", "if (w->glab && w->glab[img[0]] != w->plab[0]) continue;", ";"),
     ("root_range_shifted", "img[0] = (int32_t)(w->root_begin + i * w->root_stride);",
      "img[0] = (int32_t)(w->root_begin + i * w->root_stride - (i > 0));"),   # stays in range
+    ("entry_range_shifted", "int64_t x = w->entry_begin + i;",
+     "int64_t x = w->entry_begin + i - (i > 0 && i + 1 == (long)(w->entry_end - w->entry_begin));"),
+    ("entry_row_off_by_one", "if (w->row_ptr[mid] <= e) lo = mid; else hi = mid - 1;",
+     "if (w->row_ptr[mid] < e) lo = mid; else hi = mid - 1;"),
+    ("entry_skips_depth_one_checks", "if (!admit(w, 1, img, w->col[x])) continue;", ";"),
     ("directed_ignores_arc_direction", "good = w->chk_fwd[d][c] ? arc_present(w, o, v) : arc_present(w, v, o);",
      "good = arc_present(w, o, v) || arc_present(w, v, o);"),
     ("directed_keeps_repeated_arcs", "if (uniq == 0 || fwd[i] != fwd[uniq - 1]) fwd[uniq++] = fwd[i];",
@@ -99,6 +104,20 @@ def battery():
         check("restricted_times_aut", restricted * 2 == oracle.count_maps(house, g30))
         _, listed = oracle.list_restricted(house, sched, rs, g30)
         check("listing", listed == restricted)
+        # entry ranges: one root's row gives that root's count; cuts of all
+        # entries add up to the whole restricted count
+        r = int(np.argmax(np.diff(g30.row_ptr)))
+        row = oracle.count_restricted_entries(house, sched, rs, g30, g30.row_ptr[r], g30.row_ptr[r + 1])
+        check("entry_row", row == oracle.count_restricted(house, sched, rs, g30, root_begin=r, root_end=r + 1))
+        cuts = [0, 3, 50, 51, 97, int(g30.row_ptr[-1])]
+        parts = sum(oracle.count_restricted_entries(house, sched, rs, g30, a, b) for a, b in zip(cuts, cuts[1:]))
+        check("entry_cuts", parts == restricted)
+        # a restriction acting at the second searched vertex: triangles with
+        # id(0) > id(1) > id(2) in search order (0, 1, 2), over entry cuts
+        tri = named_pattern("triangle")
+        tparts = sum(oracle.count_restricted_entries(tri, (0, 1, 2), [(0, 1), (1, 2)], g30, a, b)
+                     for a, b in zip(cuts, cuts[1:]))
+        check("entry_restriction", tparts == oracle.triangles(g30))
         a, b = 3, 4
         gl = [0] * a + [1] * b
         check("labels", oracle.count_labeled(named_pattern("c4"), [0, 1, 0, 1], bipartite(a, b), gl)

@@ -410,3 +410,21 @@ def test_labeled_brute_force(seed):
                   if all(p[q[x], q[y]] for x, y in pe) and all(pl[q[x]] == pl[x] for x in range(k)))
         assert oracle.aut_count_labeled(p, pl) == aut
         assert oracle.count_labeled(p, pl, g, gl) == maps // aut
+
+
+def test_entry_ranges_partition_the_restricted_count():
+    """The restricted count over CSR entry ranges: a root's row gives the
+    root's count, and any cut of all entries adds up to the whole count."""
+    for seed, pname in [(3, "house"), (4, "k4"), (5, "c5"), (6, "diamond")]:
+        s, d = er_edges(40, 260, seed=seed)
+        g = oracle.build_csr(40, s, d)
+        adj = named_pattern(pname)
+        sched = pr.efficient_schedules(adj.tolist())[0][0]
+        rs = pr.restriction_sets(adj.tolist())[-1]
+        whole = oracle.count_restricted(adj, sched, rs, g)
+        nnz = int(g.row_ptr[-1])
+        cuts = [0, 1, 7, nnz // 2, nnz - 3, nnz]
+        assert sum(oracle.count_restricted_entries(adj, sched, rs, g, a, b) for a, b in zip(cuts, cuts[1:])) == whole
+        for r in (0, 5, 39):
+            assert oracle.count_restricted_entries(adj, sched, rs, g, g.row_ptr[r], g.row_ptr[r + 1]) == \
+                oracle.count_restricted(adj, sched, rs, g, root_begin=r, root_end=r + 1)

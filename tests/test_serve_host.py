@@ -27,13 +27,20 @@ class FakeSched:
         self.k = adj.shape[0]
         self.key = adj.tobytes()
 
+    def set_iep(self, enable=True):
+        return 0
+
+    def iep(self, idx=0):
+        return 0, 1
+
 
 class FakeNative:
     """Each slice advances every job by `per_slice` tasks; a task of a
     k-vertex pattern counts k. A pattern with a self loop fails planning; a
     job whose task range reaches `poison_task` is abandoned (next = -1)."""
 
-    def __init__(self, per_slice=7, poison_task=None, fail_launch=False):
+    def __init__(self, per_slice=7, poison_task=None, fail_launch=False, plan_s=0.0):
+        self.plan_s = plan_s
         self.per_slice = per_slice
         self.poison_task = poison_task
         self.fail_launch = fail_launch
@@ -47,6 +54,7 @@ class FakeNative:
         return adj
 
     def gp_schedule(self, pattern, graph, top_k=1, stream=None):
+        time.sleep(self.plan_s)              # a slow planner
         return FakeSched(pattern)
 
     def gp_count_scratch_bytes(self, graph, sched, idx):
@@ -55,10 +63,17 @@ class FakeNative:
     def make_opts(self, **kw):
         return kw
 
-    def gp_count_batch_ranges(self, graphs, scheds, idx, begin, end, opts, stream=None):
+    def gp_count_batch_ranges(self, graphs, scheds, idx, begin, end, opts, stream=None, raw=None):
+        st, out, nxt = self._ranges(scheds, begin, end)
+        if raw is not None:
+            raw[0::2] = out
+            raw[1::2] = 0
+        return st, out, nxt
+
+    def _ranges(self, scheds, begin, end):
         with self.lock:
             self.launches += 1
-            self.max_batch_seen = max(self.max_batch_seen, len(graphs))
+            self.max_batch_seen = max(self.max_batch_seen, len(scheds))
         if self.fail_launch:
             raise RuntimeError("launch failed")
         out, nxt = [], []
@@ -191,7 +206,7 @@ class FakeCursor(FakeNative):
         self.budget = budget
         self.cost = cost
 
-    def gp_count_batch_ranges(self, graphs, scheds, idx, begin, end, opts, stream=None):
+    def _ranges(self, scheds, begin, end):
         self.launches += 1
         left = self.budget
         out, nxt = [], []
@@ -234,3 +249,30 @@ def test_heavy_jobs_do_not_starve_the_rest(fake, monkeypatch):
     assert all(isinstance(r.error, TimeoutError) for r in heavy)    # max_slices
     # the heavy jobs' windows shrank below their first quota
     assert all(r.quota < 4096 for r in heavy)
+
+
+def test_latency_runs_from_arrival_and_planning_does_not_block_submit(fake):
+    """A slow planner: submit() returns at once for every client, and each
+    latency is measured from the arrival time (stamped before the lock, or
+    given), so it includes the time spent waiting for the planner."""
+    fake(per_slice=1000, plan_s=0.2)
+    srv = serve.Server({"a": FakeGraph(10)}, slice_ms=1.0)
+    try:
+        t0 = time.perf_counter()
+        reqs, took = [], []
+        for k in (3, 4, 5, 6):
+            a = time.perf_counter()
+            reqs.append(srv.submit("a", adj_k(k)))
+            took.append(time.perf_counter() - a)
+        given = srv.submit("a", adj_k(7), arrival=t0)
+        wait_all(reqs + [given])
+    finally:
+        srv.close()
+    assert max(took) < 0.1                       # never waited for the planner
+    assert all(r.arrival >= t0 and r.arrival - t0 < 0.1 for r in reqs)
+    # four distinct patterns planned one after another at 0.2 s each: the
+    # last one waited behind the others and its latency shows it
+    lat = sorted(r.latency for r in reqs)
+    assert lat[-1] >= 0.6
+    assert given.arrival == t0 and given.latency >= 0.8
+    assert [r.count for r in reqs] == [30, 40, 50, 60]
