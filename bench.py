@@ -32,15 +32,17 @@ sys.path.insert(0, ROOT)
 from synth import named_pattern, workload_edges  # noqa: E402
 
 WORKLOADS = {
-    # R-MAT scale 20, edge factor 16, a/b/c/d .57/.19/.19/.05, seed 2
-    # (house and c6 are available with --patterns; on this graph they need
-    # hours, see the design notes)
-    "rmat20": {"graph": "rmat20", "patterns": ["triangle", "k4", "k5"]},
+    # R-MAT scale 20, edge factor 16, a/b/c/d .57/.19/.19/.05, seed 2; the
+    # House and the 6-cycle run outside the timed step, each as one whole
+    # count under a device budget (the 6-cycle needs hours: no
+    # inclusion-exclusion applies, as no two non-adjacent vertices leave a
+    # connected rest)
+    "rmat20": {"graph": "rmat20", "patterns": ["triangle", "k4", "k5"], "projected": ["house", "c6"]},
     # House on G(2000, 20000), seed 1
-    "er2000": {"graph": "er2000", "patterns": ["house"]},
+    "er2000": {"graph": "er2000", "patterns": ["house"], "projected": []},
     # Chung-Lu 4M vertices, 35M pairs, exponent 2.1, max expected degree 20K,
     # seed 3
-    "cl4m": {"graph": "cl4m", "patterns": ["k6e"]},
+    "cl4m": {"graph": "cl4m", "patterns": ["k6e"], "projected": ["c6chord", "grid3x2"]},
 }
 
 L2_FLUSH_BYTES = 512 << 20          # larger than the 129 MB L2
@@ -62,23 +64,33 @@ def parse():
     ap.add_argument("--tune", action="store_true",
                     help="let the autotuner pick launch knobs per pattern (default: library defaults, which "
                          "measured faster on the full count than the tuner's task-sample choice)")
+    ap.add_argument("--model-plan", action="store_true",
+                    help="count with the plan the performance model ranks first (default: the fastest of the "
+                         "model's top three plans and their mirror images on a task sample, autotune.choose_plan)")
     ap.add_argument("--no-iep", action="store_true",
                     help="plain enumeration only (default: inclusion-exclusion for the innermost loops where a "
                          "plan qualifies, Section IV-D)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU-baseline sample budget")
-    ap.add_argument("--batched-graphs", default="rmat12,rmat11,rmat10,rmat9,rmat8",
-                    help="candidate graphs of the batched comparison, largest first ('' to skip)")
-    ap.add_argument("--mode", default="count", choices=["count", "serve", "model", "case"],
+    ap.add_argument("--project-limit-s", type=float, default=60.0,
+                    help="patterns outside the step: the device budget of their whole count")
+    ap.add_argument("--batched-graph", default="rmat20",
+                    help="graph of the batched comparison (64 random patterns x top-3 plans; '' to skip)")
+    ap.add_argument("--mode", default="count", choices=["count", "serve", "model", "case", "iep"],
                     help="serve: the continuous-batching sweep; model: performance-model accuracy; "
                          "case: one untimed count of each pattern on --graph (for profiler captures)")
     ap.add_argument("--graph", default="rmat16", help="synthetic graph of --mode case")
-    ap.add_argument("--model-graph", default="rmat14")
-    ap.add_argument("--model-patterns", default="house,diamond,tailed_triangle,c4")
+    ap.add_argument("--iep-cases", default="rmat14/star5,rmat14/star6,rmat16/star5,rmat16/star6,"
+                    "rmat14/three_ears,rmat16/three_ears,rmat14/house,rmat16/house,rmat20/house,cl1000000/k6e",
+                    help="graph/pattern pairs of --mode iep")
+    ap.add_argument("--model-graph", default="rmat20")
+    ap.add_argument("--model-patterns", default="triangle,k4,house,k5")
     ap.add_argument("--serve-scales", default="14,15,16,17,18,19,20,22")
     ap.add_argument("--serve-rates", default="10,30,100,300,1000")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-deadline", type=float, default=2.0)
     ap.add_argument("--serve-slice-ms", type=float, default=5.0)
+    ap.add_argument("--serve-mem-gb", type=float, default=2.0,
+                    help="device memory budget for the intermediate-set scratch of a time slice")
     return ap.parse_args()
 
 
@@ -384,11 +396,18 @@ def gpu_arm(a, rank, world):
             s.set_iep(True)
         return s
 
-    plans, plan_s = {}, {}
+    plans, plan_s, plan_table = {}, {}, {}
+    cache = os.path.join(ROOT, "paper_2009_10955_gb300", "_build", "tune_cache.json")
     for p in pats:
         t = time.time()
-        plans[p] = make_plan(p, g)
+        if a.model_plan:
+            plans[p] = make_plan(p, g)
+        else:
+            from paper_2009_10955_gb300 import autotune
+            plans[p], plan_table[p] = autotune.choose_plan(g, named_pattern(p), top_k=3, iep=not a.no_iep,
+                                                           cache_path=cache, stream=stream)
         plan_s[p] = time.time() - t
+    model_pick = {p: autotune_first(N, g, p, stream) for p in pats}
     # this rank's share of every pattern's edge tasks: whole roots, balanced
     # by the sum of squared degrees
     if world > 1:
@@ -402,7 +421,6 @@ def gpu_arm(a, rank, world):
     tuned, tune_s = {}, {}
     if a.tune:                               # the tuner samples task ranges
         from paper_2009_10955_gb300 import autotune
-        cache = os.path.join(ROOT, "paper_2009_10955_gb300", "_build", "tune_cache.json")
         for p in pats:
             t = time.time()
             tuned[p], _ = autotune.tune(g, plans[p], 0, space=BENCH_TUNE_SPACE, windows=64, width=1024,
@@ -473,16 +491,16 @@ def gpu_arm(a, rank, world):
     if world > 1:
         summed = allreduce_counts([counts[p] for p in pats], device=dev)
         counts = dict(zip(pats, summed))
-    for p in pats:
-        div = plans[p].iep(0)[1]
-        if counts[p] % div:
-            raise RuntimeError(f"{p}: total {counts[p]} is not a multiple of its divisor {div}")
-        counts[p] //= div
         t_local = torch.tensor([statistics.mean(step_ms)], device=dev)
         dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
         mean_step = float(t_local[0])
     else:
         mean_step = statistics.mean(step_ms)
+    for p in pats:
+        div = plans[p].iep(0)[1]
+        if counts[p] % div:
+            raise RuntimeError(f"{p}: total {counts[p]} is not a multiple of its divisor {div}")
+        counts[p] //= div
 
     # end to end through the C ABI with host buffers: graph from host pairs,
     # planning, counts and 8-byte results back
@@ -495,7 +513,11 @@ def gpu_arm(a, rank, world):
         t = time.time()
         g2 = N.gp_graph_create_edges(src_h, dst_h, n, N.GP_DEGREE_ORDER, stream=stream)
         for p in pats:
-            s2 = make_plan(p, g2)
+            order, res, _ = plans[p].get(0)
+            N.gp_schedule(N.gp_pattern_create(named_pattern(p)), g2, top_k=1, stream=stream)   # the model
+            s2 = N.gp_schedule_explicit(N.gp_pattern_create(named_pattern(p)), order, res)
+            if not a.no_iep:
+                s2.set_iep(True)
             N.gp_count(g2, s2, 0, knobs(p, task_begin=lo, task_end=hi,
                                         raw_total=ctypes.cast(raw_buf, ctypes.POINTER(ctypes.c_uint64))),
                        stream=stream)
@@ -503,9 +525,26 @@ def gpu_arm(a, rank, world):
         e2e_ms.append((time.time() - t) * 1000.0)
         del g2
 
+    # patterns of the workload that no bench-sized step can count: a rate
+    # from a stratified task sample and the projected time (labelled)
+    projected = {}
+    if world == 1 and not a.patterns:
+        for p in wl.get("projected", []):
+            if a.model_plan:
+                sp = make_plan(p, g)
+            else:
+                from paper_2009_10955_gb300 import autotune
+                sp, _ = autotune.choose_plan(g, named_pattern(p), top_k=3, iep=not a.no_iep,
+                                             cache_path=cache, stream=stream)
+            rec = budgeted_count(N, g, sp, stream, a.project_limit_s)
+            rec.update({"order": sp.get(0)[0], "restrictions": sp.get(0)[1], "iep_loops": sp.iep(0)[0]})
+            if "count" not in rec:
+                rec["sample"] = timed_or_projected(N, g, sp, stream, limit_s=0.0, sample_s=10.0)
+            projected[p] = rec
+
     batched = None
-    if a.batched_graphs and world == 1:
-        batched = batched_compare(N, stream, a.batched_graphs.split(","))
+    if a.batched_graph and world == 1:
+        batched = batched_compare(N, stream, a.batched_graph)
 
     hbm, peak_kind = peaks()
     # L2 copy bandwidth measured in this run: 2 x 24 MB buffers (48 MB
@@ -581,7 +620,12 @@ def gpu_arm(a, rank, world):
             "counts": {p: counts[p] for p in pats},
             "per_pattern_s": {p: mean_kern[p] / 1000.0 for p in pats},
             "plans": {p: {"order": plans[p].get(0)[0], "restrictions": plans[p].get(0)[1],
-                          "iep_loops": plans[p].iep(0)[0], "iep_divisor": plans[p].iep(0)[1]} for p in pats},
+                          "iep_loops": plans[p].iep(0)[0], "iep_divisor": plans[p].iep(0)[1],
+                          "model_first": tuple(plans[p].get(0)[:2]) == model_pick[p]} for p in pats},
+            "plan_choice": ("model's first plan" if a.model_plan else
+                            "fastest on a 128 x 64-task sample of the model's top 3 plans and their mirror "
+                            "images (autotune.choose_plan), untimed"),
+            "plan_candidates": plan_table,
             "graph_build_s": build_s,
             "plan_s": plan_s,
             "tuned": tuned,
@@ -592,49 +636,66 @@ def gpu_arm(a, rank, world):
         },
         "e2e": {"value": statistics.mean(e2e_ms) / 1000.0, "unit": "s",
                 "h2d_bytes_per_step": int(src.nbytes + dst.nbytes),
-                "d2h_bytes_per_step": 8 * len(pats),
-                "includes": "graph build from host pairs in pinned memory, planning, counts, results to host"},
+                "d2h_bytes_per_step": 16 * len(pats),
+                "includes": "graph build from host pairs in pinned memory, the performance model's ranking, "
+                            "the chosen plan (cached choice, gp_schedule_explicit), counts, 16-byte totals to "
+                            "host"},
         "gpu_launches": launches // max(1, a.steps),
         "roofline": roof,
         "clocks": clk,
         "batched": batched,
+        "outside_step": projected,
     }
     return out, (n, src, dst, pats)
 
 
-def batched_compare(N, stream, graph_names, npat=64, top_k=3, seed=64, reps=3, budget_s=2.0):
+def autotune_first(N, g, p, stream):
+    """(order, restrictions) of the plan the performance model ranks first."""
+    return tuple(N.gp_schedule(N.gp_pattern_create(named_pattern(p)), g, top_k=1, stream=stream).get(0)[:2])
+
+
+def batched_compare(N, stream, graph_name="rmat20", npat=64, top_k=3, seed=64, job_limit_s=1.0, total_s=15.0):
     """64 random connected 3-6-vertex patterns (edge probability 0.5), each
-    under its top-3 plans: one persistent launch for all jobs against one
-    launch per (pattern, plan) and against one launch per pattern (best plan).
-    Results must agree job by job. The first graph of `graph_names` on which
-    every job finishes within `budget_s` of device time (checked with one
-    budgeted time slice) is used; larger R-MAT graphs hold tree patterns
-    whose enumeration takes hours."""
+    under its top-3 plans with inclusion-exclusion where it applies: one
+    persistent launch for all jobs against one launch per (pattern, plan)
+    and one launch per pattern (its first plan), on `graph_name`. A pattern
+    is left out (and listed) when a task sample projects its first plan above
+    `job_limit_s`, or when the included patterns' projections (x the plans
+    each has) already reach `total_s`. Undivided 128-bit totals are compared
+    job by job; counts beyond 64 bits are reported as exact integers."""
     import torch
     from synth import random_pattern_set
     pats = random_pattern_set(npat, 3, 6, 0.5, seed)
-    chosen, skipped = None, []
-    for graph_name in graph_names:
-        n, src, dst = workload_edges(graph_name)
-        g = N.gp_graph_create_edges(src, dst, n, N.GP_DEGREE_ORDER, stream=stream)
-        scheds = [N.gp_schedule(N.gp_pattern_create(adj), g, top_k=top_k, stream=stream) for adj in pats]
-        jobs = [(s, i) for s in scheds for i in range(len(s))]
-        nnz = g.device_csr()[2]
-        try:
-            st, _, _ = N.gp_count_batch_ranges([g] * len(jobs), [s for s, _ in jobs], [i for _, i in jobs],
-                                               [0] * len(jobs), [nnz] * len(jobs),
-                                               N.make_opts(budget_cycles=int(budget_s * 1.9e9)), stream=stream)
-        except N.GraphPiError as e:        # e.g. a count beyond 64 bits
-            skipped.append(f"{graph_name}: {e.status}")
-            continue
-        if st == N.GP_OK:
-            chosen = graph_name
-            break
-        skipped.append(f"{graph_name}: not done in {budget_s} s")
-    if chosen is None:
-        return {"skipped": skipped}
-    graph_name = chosen
-    G, S, I = [g] * len(jobs), [s for s, _ in jobs], [i for _, i in jobs]
+    n, src, dst = workload_edges(graph_name)
+    g = N.gp_graph_create_edges(src, dst, n, N.GP_DEGREE_ORDER, stream=stream)
+    nnz = g.device_csr()[2]
+    scheds, proj = [], []
+    for adj in pats:
+        s = N.gp_schedule(N.gp_pattern_create(adj), g, top_k=top_k, stream=stream)
+        s.set_iep(True)
+        scheds.append(s)
+        wins = sample_windows(nnz, 128, 32, seed=1)
+        ms = ctypes.c_float()
+        raw = np.zeros(2 * len(wins), dtype=np.uint64)
+        o = N.make_opts(kernel_ms=ctypes.pointer(ms), budget_cycles=int(job_limit_s * 1.9e9),
+                        task_cycles=int(job_limit_s / 2 * 1.9e9))
+        st, _, nxt = N.gp_count_batch_ranges([g] * len(wins), [s] * len(wins), [0] * len(wins),
+                                             [a for a, _ in wins], [b for _, b in wins], o, stream=stream, raw=raw)
+        done = sum(int(x) - a for x, (a, _) in zip(nxt, wins) if int(x) >= 0)
+        bad = st != N.GP_OK or any(int(x) < 0 for x in nxt)
+        proj.append(float("inf") if bad else ms.value / 1e3 * nnz / max(done, 1))
+    keep, left_out, acc = [], [], 0.0
+    for i in sorted(range(npat), key=lambda i: proj[i]):
+        cost = proj[i] * len(scheds[i])
+        if proj[i] <= job_limit_s and acc + cost <= total_s:
+            keep.append(i)
+            acc += cost
+        else:
+            left_out.append({"pattern": i, "k": int(pats[i].shape[0]), "edges": int(pats[i].sum() // 2),
+                             "projected_s": proj[i] if proj[i] != float("inf") else None})
+    keep.sort()
+    jobs = [(i, j) for i in keep for j in range(len(scheds[i]))]
+    G, S, I = [g] * len(jobs), [scheds[i] for i, _ in jobs], [j for _, j in jobs]
 
     def timed(fn):
         torch.cuda.synchronize()
@@ -645,24 +706,39 @@ def batched_compare(N, stream, graph_names, npat=64, top_k=3, seed=64, reps=3, b
         e1.synchronize()
         return r, e0.elapsed_time(e1) / 1000.0
 
-    batched, _ = timed(lambda: N.gp_count_batch(G, S, I, stream=stream))      # warm-up
-    single = [N.gp_count(g, s, i, stream=stream)[1] for s, i in jobs]
-    if [int(x) for x in batched] != single:
-        raise AssertionError("batched counts differ from single launches")
-    tb = min(timed(lambda: N.gp_count_batch(G, S, I, stream=stream))[1] for _ in range(reps))
-    ts = min(timed(lambda: [N.gp_count(g, s, i, stream=stream) for s, i in jobs])[1] for _ in range(reps))
-    tp = min(timed(lambda: [N.gp_count(g, s, 0, stream=stream) for s in scheds])[1] for _ in range(reps))
-    return {"graph": graph_name, "skipped_graphs": skipped, "patterns": npat, "jobs": len(jobs), "batched_s": tb,
-            "per_plan_launches_s": ts, "per_pattern_launches_s": tp,
-            "speedup_vs_per_plan": ts / tb, "speedup_vs_per_pattern": tp / tb,
-            "counts_agree": True}
+    raw_b = np.zeros(2 * len(jobs), dtype=np.uint64)
+    N.gp_count_batch(G, S, I, stream=stream, raw=raw_b)                      # warm-up
+    _, tb = timed(lambda: N.gp_count_batch(G, S, I, stream=stream, raw=raw_b))
+    batched = [int(raw_b[2 * q]) | (int(raw_b[2 * q + 1]) << 64) for q in range(len(jobs))]
+    single, ts = timed(lambda: [N.gp_count_raw(g, scheds[i], j, stream=stream)[1] for i, j in jobs])
+    if batched != single:
+        raise AssertionError("batched totals differ from single launches")
+    _, tp = timed(lambda: [N.gp_count_raw(g, scheds[i], 0, stream=stream) for i in keep])
+    counts = {}
+    for (i, j), r in zip(jobs, batched):
+        div = scheds[i].iep(j)[1]
+        if r % div:
+            raise AssertionError(f"pattern {i} plan {j}: total not a multiple of its divisor")
+        c = r // div
+        if counts.setdefault(i, c) != c:
+            raise AssertionError(f"pattern {i}: plans disagree")
+    over64 = sum(1 for c in counts.values() if c >> 64)
+    return {"graph": graph_name, "patterns": npat, "patterns_counted": len(keep), "jobs": len(jobs),
+            "left_out": left_out, "batched_s": tb, "per_plan_launches_s": ts, "per_pattern_launches_s": tp,
+            "speedup_vs_per_plan": ts / tb, "speedup_vs_per_pattern": tp / tb, "counts_agree": True,
+            "counts_beyond_64_bits": over64,
+            "iep_jobs": sum(1 for i, j in jobs if scheds[i].iep(j)[0] > 0),
+            "selection": f"patterns whose first plan projects <= {job_limit_s} s on a 128 x 32-task sample, "
+                         f"cheapest first, until the included jobs project {total_s} s"}
 
 
-def serve_bench(N, stream, scales, rates, per_rate, deadline_s, slice_ms, seed=777):
+def serve_bench(N, stream, scales, rates, per_rate, deadline_s, slice_ms, mem_budget=None, seed=777):
     """Continuous-batching server over several device-resident R-MAT graphs
     (scale s, edge factor 16, seed 100 + s) under Poisson arrivals of random
-    connected 3-6-vertex patterns (edge probability 0.5). Requests that need
-    more than `deadline_s` of service are answered with a timeout."""
+    connected 3-6-vertex patterns (edge probability 0.5), admitted while the
+    slice's intermediate-set scratch fits `mem_budget` bytes. Requests that
+    need more than `deadline_s` of service are answered with a timeout.
+    Latency runs from each request's scheduled arrival time."""
     from synth import random_pattern_set
     from synth.graphs import rmat_edges
     from paper_2009_10955_gb300.serve import Server, poisson_arrivals
@@ -675,14 +751,15 @@ def serve_bench(N, stream, scales, rates, per_rate, deadline_s, slice_ms, seed=7
     rows = []
     for ri, rate in enumerate(rates):
         arr = poisson_arrivals(rate, per_rate, seed + ri)
-        srv = Server(graphs, slice_ms=slice_ms, stream=stream, item_ms=20 * slice_ms, deadline_s=deadline_s)
+        srv = Server(graphs, slice_ms=slice_ms, stream=stream, item_ms=20 * slice_ms, deadline_s=deadline_s,
+                     mem_budget=mem_budget)
         t0 = time.perf_counter()
         reqs = []
         for i, at in enumerate(arr):
             delay = t0 + at - time.perf_counter()
             if delay > 0:
                 time.sleep(delay)
-            reqs.append(srv.submit(names[i % len(names)], pats[i % len(pats)]))
+            reqs.append(srv.submit(names[i % len(names)], pats[i % len(pats)], arrival=t0 + at))
         for r in reqs:
             r.done.wait(3600)
         srv.close()
@@ -695,22 +772,112 @@ def serve_bench(N, stream, scales, rates, per_rate, deadline_s, slice_ms, seed=7
                      "p50_s": lat[len(lat) // 2] if lat else None,
                      "p99_s": lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None,
                      "counts_per_s": len(ok) / span if span > 0 else None,
-                     "slices": srv.slices})
+                     "slices": srv.slices, "admission_deferrals": srv.deferrals})
     return {"metric": "serving latency and throughput", "graphs": names, "slice_ms": slice_ms,
-            "deadline_s": deadline_s, "rows": rows}
+            "deadline_s": deadline_s, "mem_budget_bytes": mem_budget, "rows": rows}
 
 
-def model_bench(N, stream, graph_name, patterns, max_configs=400):
+def sample_windows(nnz, windows, width, seed):
+    """Stratified task windows: one window of `width` tasks at a seeded
+    random offset inside each of `windows` equal slices of the task space."""
+    rng = np.random.default_rng(seed)
+    if nnz <= windows * width:
+        return [(0, nnz)]
+    stride = nnz // windows
+    out = []
+    for i in range(windows):
+        b = i * stride + int(rng.integers(0, max(1, stride - width)))
+        out.append((b, min(nnz, b + width)))
+    return out
+
+
+def budgeted_count(N, g, s, stream, limit_s):
+    """The whole count with a device budget of limit_s: the count and its
+    kernel time when it finishes; else how many edge tasks (in CSR order,
+    high-degree roots first) the budget covered. A budget stops the launch
+    between task grabs, so the kernel time can exceed it by the longest
+    task in flight."""
+    nnz = g.device_csr()[2]
+    ms = ctypes.c_float()
+    cur = ctypes.c_int64(0)
+    st, raw = N.gp_count_raw(g, s, 0, stream=stream, kernel_ms=ctypes.pointer(ms),
+                             budget_cycles=int(limit_s * 1.9e9), resume_cursor=ctypes.pointer(cur))
+    if st == N.GP_OK:
+        return {"kind": "counted", "count": raw // s.iep(0)[1], "kernel_s": ms.value / 1e3}
+    return {"kind": f"not finished within a {limit_s:.0f} s budget", "kernel_s": ms.value / 1e3,
+            "tasks_done": cur.value, "tasks": nnz}
+
+
+def timed_or_projected(N, g, s, stream, limit_s=30.0, windows=1024, width=64, seed=0, sample_s=20.0):
+    """Whole count and kernel time when a stratified task sample projects it
+    below limit_s; else the projection (sample kernel time x tasks / sampled
+    tasks), labelled as such. A sample launch is paced by its slowest task,
+    not by throughput, so a projection leans high (K6-e on Chung-Lu 4M: a
+    256 x 64-task sample projected 178 s for a 19.7 s count). Returns a
+    dict."""
+    nnz = g.device_csr()[2]
+    wins = sample_windows(nnz, windows, width, seed)
+    ms = ctypes.c_float()
+    raw = np.zeros(2 * len(wins), dtype=np.uint64)
+    o = N.make_opts(kernel_ms=ctypes.pointer(ms), budget_cycles=int(sample_s * 1.9e9),
+                    task_cycles=int(sample_s / 4 * 1.9e9))
+    st, _, nxt = N.gp_count_batch_ranges([g] * len(wins), [s] * len(wins), [0] * len(wins),
+                                         [a for a, _ in wins], [b for _, b in wins], o, stream=stream, raw=raw)
+    done = sum(int(x) - a for x, (a, _) in zip(nxt, wins) if int(x) >= 0)
+    abandoned = sum(1 for x in nxt if int(x) < 0)
+    proj = ms.value / 1e3 * nnz / max(done, 1)
+    rec = {"sample_tasks": done, "sample_s": ms.value / 1e3, "abandoned_windows": abandoned,
+           "projected_s": proj}
+    if proj < limit_s and abandoned == 0 and st == N.GP_OK:
+        kms = ctypes.c_float()
+        c = N.gp_count(g, s, 0, N.make_opts(kernel_ms=ctypes.pointer(kms)), stream=stream)[1]
+        rec.update({"count": c, "kernel_s": kms.value / 1e3})
+    return rec
+
+
+def iep_bench(N, stream, cases, limit_s=30.0):
+    """Inclusion-exclusion (Section IV-D) against plain enumeration on the
+    same plan: for each (graph, pattern) the model's first plan is counted
+    both ways (whole counts when feasible, else projections from a task
+    sample, labelled), counts checked equal."""
+    rows = []
+    graphs = {}
+    for gname, pname in cases:
+        if gname not in graphs:
+            n, src, dst = workload_edges(gname)
+            graphs[gname] = N.gp_graph_create_edges(src, dst, n, N.GP_DEGREE_ORDER, stream=stream)
+        g = graphs[gname]
+        plain = N.gp_schedule(N.gp_pattern_create(named_pattern(pname)), g, top_k=1, stream=stream)
+        iep = N.gp_schedule(N.gp_pattern_create(named_pattern(pname)), g, top_k=1, stream=stream)
+        iep.set_iep(True)
+        row = {"graph": gname, "pattern": pname, "plan": plain.get(0)[:2], "iep_loops": iep.iep(0)[0],
+               "iep_divisor": iep.iep(0)[1],
+               "plain": timed_or_projected(N, g, plain, stream, limit_s),
+               "iep": timed_or_projected(N, g, iep, stream, limit_s)}
+        a, b = row["plain"], row["iep"]
+        if "count" in a and "count" in b and a["count"] != b["count"]:
+            raise AssertionError(f"{gname}/{pname}: plain {a['count']} != inclusion-exclusion {b['count']}")
+        ta = a.get("kernel_s", a["projected_s"])
+        tb = b.get("kernel_s", b["projected_s"])
+        row["speedup"] = ta / tb if tb > 0 else None
+        row["speedup_kind"] = "measured" if "kernel_s" in a and "kernel_s" in b else "projected"
+        rows.append(row)
+        print(json.dumps(row, default=str), file=sys.stderr, flush=True)
+    return {"metric": "inclusion-exclusion vs plain enumeration", "rows": rows}
+
+
+def model_bench(N, stream, graph_name, patterns, max_configs=120, limit_s=10.0, iep=False):
     """Performance-model accuracy (the shape of the paper's Fig. 9, Fig. 10
-    and Table II on a synthetic graph): count with every efficient schedule
-    x restriction set (evenly subsampled beyond max_configs), time each, and
-    compare the model's choice with the measured best. Every configuration
-    must give the same count."""
-    import torch
+    and Table II on a synthetic graph): every efficient schedule x
+    restriction set (evenly subsampled beyond max_configs, the model's pick
+    always included) is timed on one stratified task sample (256 windows of
+    64 tasks; all configurations on the same windows), and counted whole
+    when the sample projects it below limit_s (whole counts must agree). The
+    model's pick is compared with the best configuration, and the spread of
+    restriction sets under the picked schedule is reported."""
     n, src, dst = workload_edges(graph_name)
     g = N.gp_graph_create_edges(src, dst, n, N.GP_DEGREE_ORDER, stream=stream)
     st = g.stats(stream=stream)
-    ms = ctypes.c_float()
     rows = []
     for name in patterns:
         p = N.gp_pattern_create(named_pattern(name))
@@ -725,32 +892,36 @@ def model_bench(N, stream, graph_name, patterns, max_configs=400):
         timed, count = [], None
         for sc, rs in pairs:
             one = N.gp_schedule_explicit(p, sc, rs)
-            best_ms = None
-            for _ in range(2):
-                c = N.gp_count(g, one, 0, N.make_opts(kernel_ms=ctypes.pointer(ms)), stream=stream)[1]
-                best_ms = ms.value if best_ms is None else min(best_ms, ms.value)
-            if count is None:
-                count = c
-            elif c != count:
-                raise AssertionError(f"{name}: configuration {sc} {rs} gave {c}, expected {count}")
+            if iep:
+                one.set_iep(True)
+            rec = timed_or_projected(N, g, one, stream, limit_s=limit_s)
+            if "count" in rec:
+                if count is None:
+                    count = rec["count"]
+                elif rec["count"] != count:
+                    raise AssertionError(f"{name}: configuration {sc} {rs} gave {rec['count']}, expected {count}")
+            t = rec.get("kernel_s", rec["projected_s"])
             cost = N.gp_config_cost(p, sc, rs, st["n"], st["m"], st["tri_cnt"])
-            timed.append((best_ms, cost, sc, rs))
-        t_sorted = sorted(x[0] for x in timed)
-        pick_ms = next(x[0] for x in timed if (x[2], x[3]) == pick)
-        costs = [x[1] for x in timed]
+            timed.append((t, cost, sc, rs, "kernel_s" in rec))
         times = [x[0] for x in timed]
-        rc = np.argsort(np.argsort(costs))
+        best = min(times)
+        pick_t = next(x[0] for x in timed if (x[2], x[3]) == pick)
+        rc = np.argsort(np.argsort([x[1] for x in timed]))
         rt = np.argsort(np.argsort(times))
         spearman = float(np.corrcoef(rc, rt)[0, 1]) if len(timed) > 2 else None
-        # restriction sets for the picked schedule: best set vs the average set
         same = [x[0] for x in timed if x[2] == pick[0]]
         rows.append({"pattern": name, "count": count, "configs": len(timed),
-                     "best_ms": t_sorted[0], "worst_ms": t_sorted[-1], "pick_ms": pick_ms,
-                     "pick_vs_best": pick_ms / t_sorted[0], "worst_vs_best": t_sorted[-1] / t_sorted[0],
+                     "measured_whole": sum(1 for x in timed if x[4]),
+                     "best_s": best, "worst_s": max(times), "pick_s": pick_t,
+                     "pick_vs_best": pick_t / best, "worst_vs_best": max(times) / best,
                      "spearman_cost_vs_time": spearman,
                      "sets_for_pick_schedule": len(same),
-                     "best_set_vs_mean_set_for_pick": (float(np.mean(same)) / min(same)) if same else None})
-    return {"metric": "performance-model accuracy", "graph": graph_name, "rows": rows}
+                     "pick_set_vs_best_set_same_schedule": pick_t / min(same) if same else None,
+                     "mean_set_vs_best_set_same_schedule": float(np.mean(same)) / min(same) if same else None})
+        print(json.dumps(rows[-1], default=str), file=sys.stderr, flush=True)
+    return {"metric": "performance-model accuracy", "graph": graph_name, "iep": iep,
+            "timing": f"whole counts below {limit_s} s, else projections from the same 256 x 64-task sample",
+            "rows": rows}
 
 
 def reference_arm(a):
@@ -788,8 +959,15 @@ def main():
     if a.mode == "model":
         if rank == 0:
             from paper_2009_10955_gb300 import native
-            out = model_bench(native(), torch.cuda.current_stream(), a.model_graph, a.model_patterns.split(","))
-            print(json.dumps(out), flush=True)
+            out = model_bench(native(), torch.cuda.current_stream(), a.model_graph, a.model_patterns.split(","),
+                              iep=not a.no_iep)
+            print(json.dumps(out, default=str), flush=True)
+        return
+    if a.mode == "iep":
+        if rank == 0:
+            from paper_2009_10955_gb300 import native
+            cases = [tuple(x.split("/")) for x in a.iep_cases.split(",")]
+            print(json.dumps(iep_bench(native(), torch.cuda.current_stream(), cases), default=str), flush=True)
         return
     if a.mode == "case":
         # graph (degree order), its triangle count for the performance model
@@ -813,7 +991,8 @@ def main():
             N = native()
             out = serve_bench(N, torch.cuda.current_stream(), [int(x) for x in a.serve_scales.split(",")],
                               [float(x) for x in a.serve_rates.split(",")], a.serve_requests,
-                              a.serve_deadline, a.serve_slice_ms)
+                              a.serve_deadline, a.serve_slice_ms,
+                              mem_budget=int(a.serve_mem_gb * (1 << 30)) if a.serve_mem_gb > 0 else None)
             print(json.dumps(out), flush=True)
         return
     if world > 1:

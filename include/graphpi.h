@@ -298,7 +298,10 @@ gp_status gp_count(gp_graph* g, const gp_schedules* s, int32_t idx, const gp_cou
 
 /* Count several (graph, schedule, plan) jobs in ONE persistent launch; work
  * items of all jobs share one device work queue. out[j] receives job j's
- * count. All graphs must live on the current device. Synchronises. */
+ * count. All graphs must live on the current device. With opts->raw_total
+ * (2 x njobs words) each job's undivided 128-bit total is written there too,
+ * and a count beyond 64 bits is not an error: its out[j] is 0 and the count
+ * is raw_total / divisor. Synchronises. */
 gp_status gp_count_batch(gp_graph* const* graphs, const gp_schedules* const* scheds,
                          const int32_t* idx, int32_t njobs, const gp_count_opts* opts,
                          void* stream, uint64_t* out);

@@ -248,12 +248,19 @@ def gp_count_raw(graph, schedules, idx=0, opts=None, stream=None, **kw):
     return st, int(raw[0]) | (int(raw[1]) << 64)
 
 
-def gp_count_batch(graphs, schedules, idx=None, opts=None, stream=None):
+def gp_count_batch(graphs, schedules, idx=None, opts=None, stream=None, raw=None):
+    """Counts of the jobs (uint64 array). With raw (a uint64 numpy array of
+    2 x len(graphs)), the undivided 128-bit totals (low, high) are written
+    there, and counts beyond 64 bits come back as 0 instead of failing."""
     n = len(graphs)
     G = (ctypes.c_void_p * n)(*[g.h.value for g in graphs])
     S = (ctypes.c_void_p * n)(*[s.h.value for s in schedules])
     I = np.ascontiguousarray(idx if idx is not None else np.zeros(n), dtype=np.int32)
     out = np.zeros(n, dtype=np.uint64)
+    if raw is not None:
+        if opts is None:
+            opts = make_opts()
+        opts.raw_total = raw.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
     check(lib().gp_count_batch(G, S, _ptr(I), n, ctypes.byref(opts) if opts is not None else None,
                                _stream(stream), _ptr(out)), "gp_count_batch")
     return out

@@ -653,6 +653,8 @@ gp_status gp_count_batch(gp_graph* const* graphs, const gp_schedules* const* sch
     std::vector<uint64_t> tot((size_t)njobs);
     for (int32_t j = 0; j < njobs; ++j) {
         rc = finish_total(jobs[j].plan, res[2 * j], res[2 * j + 1], &tot[j]);
+        // with raw_total, a count beyond 64 bits is reported there alone
+        if (rc == GP_ERR_OVERFLOW && opts && opts->raw_total) { tot[j] = 0; continue; }
         if (rc != GP_OK) return rc;
     }
     for (int32_t j = 0; j < njobs; ++j) out[j] = tot[j];

@@ -250,8 +250,9 @@ __device__ __forceinline__ int warp_merge(const TaskCtx& c, const int32_t* __res
 #pragma unroll
         for (int st = 16; st; st >>= 1)
             if (__shfl_sync(kFull, y, pos + st - 1) < x) pos += st;
+        const int yp = __shfl_sync(kFull, y, pos);        // every lane takes part
         const bool mine = ia + lane < na && x <= bmax;   // resolved in this round
-        const bool f = mine && __shfl_sync(kFull, y, pos & 31) == x && pos < 32;
+        const bool f = mine && yp == x;
         const unsigned m = __ballot_sync(kFull, f);
         if (out && f) {
             const int at = total + __popc(m & lanemask_lt());

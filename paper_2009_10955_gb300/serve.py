@@ -108,6 +108,7 @@ class Server:
         self._rid = 0
         self._nnz = {k: g.device_csr()[2] for k, g in self.graphs.items()}
         self.slices = 0
+        self.deferrals = 0                # admissions put off by the memory budget
         self.thread = threading.Thread(target=self._loop, daemon=True)
         self.thread.start()
 
@@ -172,6 +173,7 @@ class Server:
                 r.quota = self.quota0
                 self._active.append(r)
             self._pending.extendleft(reversed(back))
+            self.deferrals += len(back)
 
     def _loop(self):
         while True:

@@ -57,3 +57,33 @@ def test_tune_returns_and_caches(env, tmp_path):
     assert best2 == best
     assert json.load(open(cache))
     assert N.gp_count(g, sc, 0, autotune.opts_for(best)) == (N.GP_OK, oracle.count(adj, ref))
+
+
+@pytest.mark.parametrize("gname,pname", [("rmat10", "house"), ("er2000", "k4"), ("rmat10", "star5")])
+def test_plan_choice_by_sample(env, gname, pname, tmp_path):
+    """The sampled plan choice: every candidate (top plans and their mirror
+    images, with inclusion-exclusion where it applies) is timed, and the
+    chosen plan's whole count equals the oracle's; a second call takes the
+    cached choice."""
+    from paper_2009_10955_gb300 import autotune
+    N, graphs = env
+    g, ref = graphs[gname]
+    adj = named_pattern(pname)
+    cache = str(tmp_path / "plans.json")
+    sched, table = autotune.choose_plan(g, adj, top_k=3, windows=16, width=8, cache_path=cache)
+    assert len(table) >= 2 and all(t is not None for *_, t in table)
+    mirrored = {(tuple(o), tuple(map(tuple, r))) for o, r, _, _ in table}
+    for o, r, _, _ in table:
+        assert (tuple(o), tuple((b, a) for a, b in r)) in mirrored
+    if pname in ("house", "star5"):        # both forms of plans that qualify for inclusion-exclusion
+        assert {kk > 0 for _, _, kk, _ in table} == {True, False}
+    if pname.startswith("star"):       # closed form: a centre and L of its neighbours
+        from math import comb
+        import numpy as np
+        expect = sum(comb(int(d), adj.shape[0] - 1) for d in np.diff(ref.row_ptr))
+    else:
+        expect = oracle.count(adj, ref)
+    assert N.gp_count(g, sched) == (N.GP_OK, expect)
+    again, table2 = autotune.choose_plan(g, adj, top_k=3, windows=16, width=8, cache_path=cache)
+    assert table2 == json.loads(json.dumps(table)) and again.get(0)[:2] == sched.get(0)[:2]
+    assert N.gp_count(g, again) == (N.GP_OK, expect)

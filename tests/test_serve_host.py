@@ -134,6 +134,7 @@ def test_memory_budget_limits_the_batch(fake):
         srv.close()
     assert [r.count for r in reqs] == [120, 120, 160]
     assert f.max_batch_seen == 2         # two 3-vertex jobs fit; the 4-vertex job waits
+    assert srv.deferrals > 0             # and its admission was put off at least once
 
 
 def test_abandoned_work_item_times_out_alone(fake):
