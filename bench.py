@@ -75,10 +75,12 @@ def parse():
                     help="patterns outside the step: the device budget of their whole count")
     ap.add_argument("--batched-graph", default="rmat20",
                     help="graph of the batched comparison (64 random patterns x top-3 plans; '' to skip)")
-    ap.add_argument("--mode", default="count", choices=["count", "serve", "model", "case", "iep"],
+    ap.add_argument("--mode", default="count", choices=["count", "serve", "model", "case", "iep", "directed"],
                     help="serve: the continuous-batching sweep; model: performance-model accuracy; "
                          "case: one untimed count of each pattern on --graph (for profiler captures)")
     ap.add_argument("--graph", default="rmat16", help="synthetic graph of --mode case")
+    ap.add_argument("--case-range", default="0,1",
+                    help="--mode case: the fraction range [a, b) of the edge tasks to count")
     ap.add_argument("--iep-cases", default="rmat14/star5,rmat14/star6,rmat16/star5,rmat16/star6,"
                     "rmat14/three_ears,rmat16/three_ears,rmat14/house,rmat16/house,rmat20/house,cl1000000/k6e",
                     help="graph/pattern pairs of --mode iep")
@@ -187,11 +189,12 @@ class ClockSampler:
 
 # -------------------------------------------------------------- CPU baseline
 
-def _oracle_worker(n, src, dst, name, sets, threads, q):
+def _oracle_worker(n, row_ptr, col, name, sets, threads, q):
     """Child process: time the oracle on the given root sets (begin, end,
-    stride) of the degree-ordered graph, one set after another."""
+    stride) of the degree-ordered graph (the oracle's CSR, built once by the
+    parent), one set after another."""
     import oracle
-    g, _ = oracle.degree_relabel(oracle.build_csr(n, src, dst))
+    g = oracle.Csr(n, row_ptr, col)
     q.put(("ready", 0, 0.0))
     adj = named_pattern(name)
     for b, e, st in sets:
@@ -232,9 +235,11 @@ def cpu_baseline(n, src, dst, patterns, budget_s, seed=12345, per_set=64):
     same seed, so they time the same root sets."""
     import multiprocessing as mp
     import queue as qmod
+    import oracle
     threads = os.cpu_count() or 1
     ctx = mp.get_context("spawn")
     rng = np.random.default_rng(seed)
+    og, _ = oracle.degree_relabel(oracle.build_csr(n, src, dst))
     strata = degree_strata(n, src, dst)[::-1]       # lowest degrees first
     sets = []
     for a, b, _ in strata:
@@ -245,7 +250,7 @@ def cpu_baseline(n, src, dst, patterns, budget_s, seed=12345, per_set=64):
     est, parts, lower = 0.0, [], False
     for name in patterns:
         q = ctx.Queue()
-        proc = ctx.Process(target=_oracle_worker, args=(n, src, dst, name, sets, threads, q), daemon=True)
+        proc = ctx.Process(target=_oracle_worker, args=(n, og.row_ptr, og.col, name, sets, threads, q), daemon=True)
         proc.start()
         try:
             q.get(timeout=900)                       # CSR built; the clock starts now
@@ -373,6 +378,14 @@ def recorded_traffic(workload):
     return {}
 
 
+_T0 = time.time()
+
+
+def phase(name):
+    """Progress line on stderr: seconds since start and the phase begun."""
+    print(f"[bench {time.time() - _T0:7.1f} s] {name}", file=sys.stderr, flush=True)
+
+
 def gpu_arm(a, rank, world):
     import torch
     import torch.distributed as dist
@@ -384,6 +397,7 @@ def gpu_arm(a, rank, world):
     pats = a.patterns.split(",") if a.patterns else wl["patterns"]
     n, src, dst = workload_edges(wl["graph"])
 
+    phase("graph build")
     t = time.time()
     g = N.gp_graph_create_edges(src, dst, n, N.GP_DEGREE_ORDER, stream=stream)
     torch.cuda.synchronize()
@@ -396,6 +410,7 @@ def gpu_arm(a, rank, world):
             s.set_iep(True)
         return s
 
+    phase("plans")
     plans, plan_s, plan_table = {}, {}, {}
     cache = os.path.join(ROOT, "paper_2009_10955_gb300", "_build", "tune_cache.json")
     for p in pats:
@@ -453,6 +468,7 @@ def gpu_arm(a, rank, world):
             raise RuntimeError(f"count of {p} returned status {status}")
         return int(raw_buf[0]) | (int(raw_buf[1]) << 64), e0.elapsed_time(e1), ms.value
 
+    phase("instrumented counts")
     # algorithmic work per pattern (instrumented kernel on the same paths as
     # the timed launch, untimed): list-path bytes and bitmap word operations
     algo, algo_ops = {}, {}
@@ -464,6 +480,7 @@ def gpu_arm(a, rank, world):
         N.gp_count(g, plans[p], 0, o, stream=stream)
         algo[p], algo_ops[p] = b.value, ops.value
 
+    phase("warm-up and timed steps")
     for _ in range(a.warmup):
         for p in pats:
             count(p, False)
@@ -502,6 +519,7 @@ def gpu_arm(a, rank, world):
             raise RuntimeError(f"{p}: total {counts[p]} is not a multiple of its divisor {div}")
         counts[p] //= div
 
+    phase("end to end")
     # end to end through the C ABI with host buffers: graph from host pairs,
     # planning, counts and 8-byte results back
     e2e_ms = []
@@ -528,6 +546,7 @@ def gpu_arm(a, rank, world):
     # patterns of the workload that no bench-sized step can count: a rate
     # from a stratified task sample and the projected time (labelled)
     projected = {}
+    phase("patterns outside the step")
     if world == 1 and not a.patterns:
         for p in wl.get("projected", []):
             if a.model_plan:
@@ -543,6 +562,7 @@ def gpu_arm(a, rank, world):
             projected[p] = rec
 
     batched = None
+    phase("batched comparison")
     if a.batched_graph and world == 1:
         batched = batched_compare(N, stream, a.batched_graph)
 
@@ -674,16 +694,17 @@ def batched_compare(N, stream, graph_name="rmat20", npat=64, top_k=3, seed=64, j
         s = N.gp_schedule(N.gp_pattern_create(adj), g, top_k=top_k, stream=stream)
         s.set_iep(True)
         scheds.append(s)
-        wins = sample_windows(nnz, 128, 32, seed=1)
-        ms = ctypes.c_float()
+        wins = sample_windows(nnz, 256, 32, seed=1)
         raw = np.zeros(2 * len(wins), dtype=np.uint64)
-        o = N.make_opts(kernel_ms=ctypes.pointer(ms), budget_cycles=int(job_limit_s * 1.9e9),
-                        task_cycles=int(job_limit_s / 2 * 1.9e9))
+        busy = (ctypes.c_uint64 * 2)()
+        o = N.make_opts(budget_cycles=int(job_limit_s * 1.9e9), task_cycles=int(job_limit_s / 2 * 1.9e9),
+                        busy_cycles=ctypes.cast(busy, ctypes.POINTER(ctypes.c_uint64)))
         st, _, nxt = N.gp_count_batch_ranges([g] * len(wins), [s] * len(wins), [0] * len(wins),
                                              [a for a, _ in wins], [b for _, b in wins], o, stream=stream, raw=raw)
         done = sum(int(x) - a for x, (a, _) in zip(nxt, wins) if int(x) >= 0)
         bad = st != N.GP_OK or any(int(x) < 0 for x in nxt)
-        proj.append(float("inf") if bad else ms.value / 1e3 * nnz / max(done, 1))
+        from paper_2009_10955_gb300.autotune import project_s
+        proj.append(float("inf") if bad else project_s((busy[0], busy[1]), done, nnz))
     keep, left_out, acc = [], [], 0.0
     for i in sorted(range(npat), key=lambda i: proj[i]):
         cost = proj[i] * len(scheds[i])
@@ -728,7 +749,8 @@ def batched_compare(N, stream, graph_name="rmat20", npat=64, top_k=3, seed=64, j
             "speedup_vs_per_plan": ts / tb, "speedup_vs_per_pattern": tp / tb, "counts_agree": True,
             "counts_beyond_64_bits": over64,
             "iep_jobs": sum(1 for i, j in jobs if scheds[i].iep(j)[0] > 0),
-            "selection": f"patterns whose first plan projects <= {job_limit_s} s on a 128 x 32-task sample, "
+            "selection": f"patterns whose first plan projects <= {job_limit_s} s (busy warp cycles of a "
+                         f"256 x 32-task sample) and finishes it, "
                          f"cheapest first, until the included jobs project {total_s} s"}
 
 
@@ -800,8 +822,14 @@ def budgeted_count(N, g, s, stream, limit_s):
     nnz = g.device_csr()[2]
     ms = ctypes.c_float()
     cur = ctypes.c_int64(0)
-    st, raw = N.gp_count_raw(g, s, 0, stream=stream, kernel_ms=ctypes.pointer(ms),
-                             budget_cycles=int(limit_s * 1.9e9), resume_cursor=ctypes.pointer(cur))
+    try:
+        st, raw = N.gp_count_raw(g, s, 0, stream=stream, kernel_ms=ctypes.pointer(ms),
+                                 budget_cycles=int(limit_s * 1.9e9), task_cycles=int(limit_s / 2 * 1.9e9),
+                                 resume_cursor=ctypes.pointer(cur))
+    except N.GraphPiError as e:
+        if e.status != N.GP_ERR_TIMEOUT:
+            raise
+        return {"kind": f"a single edge task outlived {limit_s / 2:.0f} s; count abandoned"}
     if st == N.GP_OK:
         return {"kind": "counted", "count": raw // s.iep(0)[1], "kernel_s": ms.value / 1e3}
     return {"kind": f"not finished within a {limit_s:.0f} s budget", "kernel_s": ms.value / 1e3,
@@ -810,22 +838,26 @@ def budgeted_count(N, g, s, stream, limit_s):
 
 def timed_or_projected(N, g, s, stream, limit_s=30.0, windows=1024, width=64, seed=0, sample_s=20.0):
     """Whole count and kernel time when a stratified task sample projects it
-    below limit_s; else the projection (sample kernel time x tasks / sampled
-    tasks), labelled as such. A sample launch is paced by its slowest task,
-    not by throughput, so a projection leans high (K6-e on Chung-Lu 4M: a
-    256 x 64-task sample projected 178 s for a 19.7 s count). Returns a
-    dict."""
+    below limit_s; else the projection, labelled as such. The projection is
+    the sample launch's busy warp cycles (each warp's cycles until it found
+    no work left, summed: the sample's total work) x (tasks / sampled tasks)
+    / (warps x clock), i.e. that work spread evenly over the full launch; a
+    sample's own duration would instead be paced by its slowest task.
+    Returns a dict."""
+    from paper_2009_10955_gb300.autotune import project_s
     nnz = g.device_csr()[2]
     wins = sample_windows(nnz, windows, width, seed)
     ms = ctypes.c_float()
     raw = np.zeros(2 * len(wins), dtype=np.uint64)
+    busy = (ctypes.c_uint64 * 2)()
     o = N.make_opts(kernel_ms=ctypes.pointer(ms), budget_cycles=int(sample_s * 1.9e9),
-                    task_cycles=int(sample_s / 4 * 1.9e9))
+                    task_cycles=int(sample_s / 4 * 1.9e9),
+                    busy_cycles=ctypes.cast(busy, ctypes.POINTER(ctypes.c_uint64)))
     st, _, nxt = N.gp_count_batch_ranges([g] * len(wins), [s] * len(wins), [0] * len(wins),
                                          [a for a, _ in wins], [b for _, b in wins], o, stream=stream, raw=raw)
     done = sum(int(x) - a for x, (a, _) in zip(nxt, wins) if int(x) >= 0)
     abandoned = sum(1 for x in nxt if int(x) < 0)
-    proj = ms.value / 1e3 * nnz / max(done, 1)
+    proj = project_s((busy[0], busy[1]), done, nnz) or float("inf")
     rec = {"sample_tasks": done, "sample_s": ms.value / 1e3, "abandoned_windows": abandoned,
            "projected_s": proj}
     if proj < limit_s and abandoned == 0 and st == N.GP_OK:
@@ -864,6 +896,47 @@ def iep_bench(N, stream, cases, limit_s=30.0):
         rows.append(row)
         print(json.dumps(row, default=str), file=sys.stderr, flush=True)
     return {"metric": "inclusion-exclusion vs plain enumeration", "rows": rows}
+
+
+DIRECTED_PATTERNS = {
+    "cycle3": [(0, 1), (1, 2), (2, 0)],
+    "feed_forward": [(0, 1), (0, 2), (1, 2)],
+    "cycle4": [(0, 1), (1, 2), (2, 3), (3, 0)],
+    "bifan": [(0, 2), (0, 3), (1, 2), (1, 3)],
+}
+
+
+def directed_bench(N, stream, scales=(14, 16, 18), reps=3):
+    """Directed patterns (the reading of an extension the paper names) on
+    R-MAT graphs taken as digraphs (each sampled pair an arc src -> dst,
+    loops and repeated arcs dropped): time of gp_dcount with the planner's
+    configuration, best of `reps` synchronous calls after one warm-up."""
+    from synth.graphs import rmat_edges
+    rows = []
+    for sc in scales:
+        src, dst = rmat_edges(sc, 16, 0.57, 0.19, 0.19, seed=2)
+        g = N.gp_dgraph_create(src, dst, 1 << sc, stream=stream)
+        st = g.stats()
+        for name, arcs in DIRECTED_PATTERNS.items():
+            k = 1 + max(max(a, b) for a, b in arcs)
+            adj = np.zeros((k, k), np.uint8)
+            for a, b in arcs:
+                adj[a, b] = 1
+            p = N.gp_dpattern_create(adj)
+            c = N.gp_dcount(g, p, stream=stream)
+            best = None
+            for _ in range(reps):
+                t = time.perf_counter()
+                c2 = N.gp_dcount(g, p, stream=stream)
+                dt = time.perf_counter() - t
+                best = dt if best is None else min(best, dt)
+                if c2 != c:
+                    raise AssertionError(f"{name} on rmat{sc}: counts differ between calls")
+            rows.append({"graph": f"rmat{sc} (directed)", "n": st["n"], "arcs": st["narcs"], "pattern": name,
+                         "count": c, "call_s": best})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    return {"metric": "directed pattern count time (s)", "rows": rows,
+            "timing": "wall time of the synchronous gp_dcount call (planning included), best of 3"}
 
 
 def model_bench(N, stream, graph_name, patterns, max_configs=120, limit_s=10.0, iep=False):
@@ -963,6 +1036,11 @@ def main():
                               iep=not a.no_iep)
             print(json.dumps(out, default=str), flush=True)
         return
+    if a.mode == "directed":
+        if rank == 0:
+            from paper_2009_10955_gb300 import native
+            print(json.dumps(directed_bench(native(), torch.cuda.current_stream())), flush=True)
+        return
     if a.mode == "iep":
         if rank == 0:
             from paper_2009_10955_gb300 import native
@@ -978,11 +1056,20 @@ def main():
             n, src, dst = workload_edges(a.graph)
             g = N.gp_graph_create_edges(src, dst, n, N.GP_DEGREE_ORDER)
             g.stats()
+            nnz = g.device_csr()[2]
+            lo_f, hi_f = (float(x) for x in a.case_range.split(","))
+            tb, te = int(nnz * lo_f), int(nnz * hi_f)
             for pn in (a.patterns or "k4").split(","):
-                sc = N.gp_schedule(N.gp_pattern_create(named_pattern(pn)), g)
-                if not a.no_iep:
-                    sc.set_iep(True)
-                print(pn, N.gp_count(g, sc, 0), flush=True)
+                if a.model_plan:
+                    sc = N.gp_schedule(N.gp_pattern_create(named_pattern(pn)), g)
+                    if not a.no_iep:
+                        sc.set_iep(True)
+                else:
+                    from paper_2009_10955_gb300 import autotune
+                    cache = os.path.join(ROOT, "paper_2009_10955_gb300", "_build", "tune_cache.json")
+                    sc, _ = autotune.choose_plan(g, named_pattern(pn), top_k=3, iep=not a.no_iep, cache_path=cache)
+                print(pn, sc.get(0)[:2], sc.iep(0),
+                      N.gp_count_raw(g, sc, 0, task_begin=tb, task_end=te if te < nnz else 0), flush=True)
             torch.cuda.synchronize()
         return
     if a.mode == "serve":
@@ -1002,6 +1089,7 @@ def main():
     out, (n, src, dst, pats) = gpu_arm(a, rank, world)
     if rank == 0:
         if world == 1 and not a.no_cpu_baseline:
+            phase("cpu baseline")
             out["cpu_baseline"] = cpu_baseline(n, src, dst, pats, a.cpu_seconds)
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -268,6 +268,12 @@ typedef struct gp_count_opts {
                                  candidate taken from a set (the bitmap
                                  counterpart of algo_bytes, which then covers the
                                  list path only)                                   */
+    uint64_t* busy_cycles;    /* host out (may be NULL), 2 words: the sum over the
+                                 launch's warps of the SM cycles each spent before it
+                                 found no work left, and the number of warps
+                                 launched. The sum measures the launch's total work
+                                 even when a few long tasks set its duration; a
+                                 count over a task sample scales it to the whole  */
 } gp_count_opts;
 
 /* gp_count_opts.flags */

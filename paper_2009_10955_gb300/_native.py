@@ -96,6 +96,7 @@ class gp_count_opts(ctypes.Structure):
         ("task_cycles", ctypes.c_int64),
         ("raw_total", ctypes.POINTER(ctypes.c_uint64)),
         ("algo_ops", ctypes.POINTER(ctypes.c_uint64)),
+        ("busy_cycles", ctypes.POINTER(ctypes.c_uint64)),
     ]
 
 

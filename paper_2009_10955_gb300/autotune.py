@@ -29,8 +29,10 @@ mirrors, each with and without inclusion-exclusion (an inclusion-exclusion
 plan gives up the bitmap subtree, which dense patterns need); the fastest on
 the sample wins. A candidate whose sample outlives a cycle limit is dropped.
 A short sample launch is paced by its slowest task rather than by
-throughput, so its time overstates the full count's time per task; the
-choice compares candidates on the same windows, which is what it needs.
+throughput, so the candidates are compared by the launch's busy warp cycles
+(each warp's cycles until it found no work left, summed), which measure the
+sample's total work however unevenly it spread; ``project_s`` turns them
+into a projected time for the whole count.
 """
 
 import ctypes
@@ -63,12 +65,18 @@ def opts_for(cfg, **extra):
                        **extra)
 
 
-def sample_ranges(nnz, windows, width):
-    """Evenly spaced task windows covering the whole task space."""
+def sample_ranges(nnz, windows, width, seed=0):
+    """Stratified task windows: one window of `width` tasks at a seeded
+    offset inside each of `windows` equal slices of the task space (every
+    task equally likely to be sampled)."""
     if nnz <= windows * width:
         return [(0, nnz)]
     step = nnz // windows
-    return [(i * step, min(nnz, i * step + width)) for i in range(windows)]
+    out = []
+    for i in range(windows):
+        off = int(((i * 0x9E3779B97F4A7C15 + seed) >> 7) % max(1, step - width))
+        out.append((i * step + off, min(nnz, i * step + off + width)))
+    return out
 
 
 def time_config(graph, sched, idx, cfg, ranges, reps=2, stream=None):
@@ -132,6 +140,16 @@ def tune(graph, sched, idx=0, space=None, windows=64, width=2048, cache_path=Non
     return best, table
 
 
+def project_s(busy, done, total, clock_hz=2.07e9):
+    """Projected time of a whole count from a sample launch: busy warp
+    cycles x (all tasks / sampled tasks) / (warps x clock), i.e. the
+    sample's total work spread evenly over the full launch's warps."""
+    cycles, warps = busy
+    if done <= 0 or warps <= 0:
+        return None
+    return cycles * (total / done) / (warps * clock_hz)
+
+
 def plan_candidates(pattern, graph, top_k=3, stream=None):
     """(order, restrictions) of the model's top_k plans and of their mirror
     images (every restriction reversed: a valid set of the same model cost),
@@ -164,7 +182,7 @@ def choose_plan(graph, adj, top_k=3, iep=True, windows=256, width=64, item_s=2.0
     st = graph.stats(with_triangles=False)
     key = json.dumps({"device": device, "n": st["n"], "m": st["m"], "max_deg": st["max_deg"],
                       "pattern": adj.tolist(), "top_k": top_k, "iep": iep, "windows": windows, "width": width,
-                      "choose_plan": 2}, sort_keys=True)
+                      "choose_plan": 3}, sort_keys=True)
     cache = {}
     if cache_path and os.path.exists(cache_path):
         with open(cache_path) as f:
@@ -189,12 +207,15 @@ def choose_plan(graph, adj, top_k=3, iep=True, windows=256, width=64, item_s=2.0
         if use_iep and sched.set_iep(True) == 0:
             continue                                    # inclusion-exclusion does not apply
         raw = np.zeros(2 * len(ranges), dtype=np.uint64)
+        busy = (ctypes.c_uint64 * 2)()
         o = N.make_opts(kernel_ms=ctypes.pointer(ms), task_cycles=int(item_s * 1.9e9),
-                        budget_cycles=int(4 * item_s * 1.9e9))
+                        budget_cycles=int(4 * item_s * 1.9e9),
+                        busy_cycles=ctypes.cast(busy, ctypes.POINTER(ctypes.c_uint64)))
         status, _, nxt = N.gp_count_batch_ranges([graph] * len(ranges), [sched] * len(ranges),
                                                  [0] * len(ranges), [a for a, _ in ranges],
                                                  [b for _, b in ranges], o, stream=stream, raw=raw)
-        t = ms.value if status == N.GP_OK else None     # stopped or abandoned: dropped
+        done = sum(b - a for a, b in ranges)
+        t = project_s((busy[0], busy[1]), done, nnz) if status == N.GP_OK else None   # stopped: dropped
         table.append((list(order), [list(r) for r in res], sched.iep(0)[0], t))
         if t is not None and (best is None or t < best[0]):
             best = (t, sched, (list(order), [list(r) for r in res], use_iep))

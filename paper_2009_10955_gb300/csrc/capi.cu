@@ -585,9 +585,9 @@ gp_status gp_count(gp_graph* g, const gp_schedules* s, int32_t idx, const gp_cou
     uint64_t bytes = 0;
     const bool want_ms = opts && opts->kernel_ms;
     int aborted = 0;
-    uint64_t ops = 0;
+    uint64_t ops = 0, busy[2] = {0, 0};
     rc = run_count(&job, 1, launch_opts(opts), static_cast<cudaStream_t>(stream), res, &done,
-                   want_ms ? &ms : nullptr, &bytes, &aborted, &ops);
+                   want_ms ? &ms : nullptr, &bytes, &aborted, &ops, busy);
     if (rc != GP_OK) return rc;
     if (aborted) return fail(GP_ERR_TIMEOUT, "a work item outlived opts.task_cycles; the count was abandoned");
     uint64_t total = 0;
@@ -601,6 +601,7 @@ gp_status gp_count(gp_graph* g, const gp_schedules* s, int32_t idx, const gp_cou
     if (want_ms) *opts->kernel_ms = ms;
     if (opts && opts->algo_bytes && (opts->flags & GP_COUNT_STATS)) *opts->algo_bytes = bytes;
     if (opts && opts->algo_ops && (opts->flags & GP_COUNT_STATS)) *opts->algo_ops = ops;
+    if (opts && opts->busy_cycles) { opts->busy_cycles[0] = busy[0]; opts->busy_cycles[1] = busy[1]; }
     if (done < job.nvirt) {
         if (opts && opts->resume_cursor) *opts->resume_cursor = job.task_begin + done;
         *out = total;
@@ -641,15 +642,16 @@ gp_status gp_count_batch(gp_graph* const* graphs, const gp_schedules* const* sch
     uint64_t bytes = 0;
     const bool want_ms = opts && opts->kernel_ms;
     std::vector<int> aborted((size_t)njobs, 0);
-    uint64_t ops = 0;
+    uint64_t ops = 0, busy[2] = {0, 0};
     rc = run_count(jobs.data(), njobs, lo, static_cast<cudaStream_t>(stream), res.data(), &done,
-                   want_ms ? &ms : nullptr, &bytes, aborted.data(), &ops);
+                   want_ms ? &ms : nullptr, &bytes, aborted.data(), &ops, busy);
     if (rc != GP_OK) return rc;
     for (int32_t j = 0; j < njobs; ++j)
         if (aborted[j]) return fail(GP_ERR_TIMEOUT, "a work item outlived opts.task_cycles; the batch was abandoned");
     if (want_ms) *opts->kernel_ms = ms;
     if (opts && opts->algo_bytes && (opts->flags & GP_COUNT_STATS)) *opts->algo_bytes = bytes;
     if (opts && opts->algo_ops && (opts->flags & GP_COUNT_STATS)) *opts->algo_ops = ops;
+    if (opts && opts->busy_cycles) { opts->busy_cycles[0] = busy[0]; opts->busy_cycles[1] = busy[1]; }
     std::vector<uint64_t> tot((size_t)njobs);
     for (int32_t j = 0; j < njobs; ++j) {
         rc = finish_total(jobs[j].plan, res[2 * j], res[2 * j + 1], &tot[j]);
@@ -695,8 +697,9 @@ gp_status gp_count_batch_ranges(gp_graph* const* graphs, const gp_schedules* con
     float ms = 0.f;
     const bool want_ms = opts && opts->kernel_ms;
     std::vector<int> aborted((size_t)njobs, 0);
+    uint64_t busy[2] = {0, 0};
     rc = run_count(jobs.data(), njobs, launch_opts(opts), static_cast<cudaStream_t>(stream), res.data(),
-                   &done, want_ms ? &ms : nullptr, nullptr, aborted.data());
+                   &done, want_ms ? &ms : nullptr, nullptr, aborted.data(), nullptr, busy);
     if (rc != GP_OK) return rc;
     for (int32_t j = 0; j < njobs; ++j)
         if (!jobs[j].plan.iep && res[2 * j + 1] && !aborted[j])
@@ -713,6 +716,7 @@ gp_status gp_count_batch_ranges(gp_graph* const* graphs, const gp_schedules* con
         all = all && !aborted[j] && p == jobs[j].ntasks;
     }
     if (want_ms) *opts->kernel_ms = ms;
+    if (opts && opts->busy_cycles) { opts->busy_cycles[0] = busy[0]; opts->busy_cycles[1] = busy[1]; }
     return all ? GP_OK : GP_PARTIAL;
 }
 

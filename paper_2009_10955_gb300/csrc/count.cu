@@ -405,6 +405,18 @@ __device__ __forceinline__ int excluded_hits(const TaskCtx& c, const GpLevel& lv
     return hits;
 }
 
+// excluded_hits with one lane per matched vertex (warp-uniform call; the
+// same value on every lane).
+__device__ __forceinline__ int excluded_hits_warp(const TaskCtx& c, const GpLevel& lv, int L, const int* v,
+                                                  Window w, List a, const List* b) {
+    bool hit = false;
+    if (c.lane < L && (lv.excl_mask >> c.lane & 1)) {
+        const int x = v[c.lane];
+        hit = x > w.lo && x < w.hi && member(c, a, x) && (!b || member(c, *b, x));
+    }
+    return __popc(__ballot_sync(kFull, hit));
+}
+
 // Contribution of the innermost loop given v[0..k-2] (warp-uniform).
 __device__ __forceinline__ void count_last(const TaskCtx& c, const int* v, Acc& acc) {
     const GpPlan& P = *c.P;
@@ -415,14 +427,14 @@ __device__ __forceinline__ void count_last(const TaskCtx& c, const int* v, Acc& 
         const List a = (P.last_base_kind == 1) ? nbr(c, v[P.last_base]) : slot(c, P.last_base);
         const List b = nbr(c, v[L - 1]);
         warp_intersect(c, a, b, w, nullptr, 0, &acc);
-        if (c.lane == 0) {
-            const List a2 = is_core(c, a.v) ? a : clip(a, w);
-            const List b2 = is_core(c, b.v) ? b : clip(b, w);
-            acc.sub((unsigned long long)excluded_hits(c, lv, L, v, w, a2, &b2));
-        }
+        const List a2 = is_core(c, a.v) ? a : clip(a, w);
+        const List b2 = is_core(c, b.v) ? b : clip(b, w);
+        const int hits = excluded_hits_warp(c, lv, L, v, w, a2, &b2);
+        if (c.lane == 0) acc.sub((unsigned long long)hits);
     } else {
         const List a = clip((lv.src_kind == 1) ? nbr(c, v[lv.src]) : slot(c, lv.src), w);
-        if (c.lane == 0) acc.add((unsigned long long)a.n - excluded_hits(c, lv, L, v, w, a, nullptr));
+        const int hits = excluded_hits_warp(c, lv, L, v, w, a, nullptr);
+        if (c.lane == 0) acc.add((unsigned long long)a.n - hits);
     }
 }
 
@@ -463,15 +475,29 @@ __device__ __forceinline__ void iep_count2(const TaskCtx& c, const int* v, Acc& 
     const List A = clip((LA.src_kind == 1) ? nbr(c, v[LA.src]) : slot(c, LA.src), wa);
     const List B = clip((LB.src_kind == 1) ? nbr(c, v[LB.src]) : slot(c, LB.src), wb);
     const Window open{-1, INT_MAX};
-    const int ab = warp_intersect(c, A, B, open, nullptr, 0, nullptr);
+    // the two sets are often one (both inner vertices adjacent to the same
+    // outer vertices, as in K6-e): then S_a ∩ S_b = S_a
+    const int ab = (A.p == B.p && A.n == B.n) ? A.n : warp_intersect(c, A, B, open, nullptr, 0, nullptr);
+    // matched vertices inside S_a, S_b and both: a matched vertex can be in a
+    // set only when the set's exclusion mask names its depth (operands and
+    // window bounds exclude it), so lane j tests v_j against S_a and lane
+    // 16 + j against S_b, all searches at once
+    const int j = c.lane & 15;
+    const bool forA = c.lane < 16;
+    const GpLevel& L = forA ? LA : LB;
+    const List S = forA ? A : B;
+    const Window w = forA ? wa : wb;
+    bool in = false;
+    if (j < da && (L.excl_mask >> j & 1)) {
+        const int x = v[j];
+        in = x > w.lo && x < w.hi && member(c, S, x);
+    }
+    const unsigned m = __ballot_sync(kFull, in);
     if (c.lane == 0) {
-        const int a = A.n - excluded_hits(c, LA, da, v, wa, A, nullptr);
-        const int b = B.n - excluded_hits(c, LB, db, v, wb, B, nullptr);
-        int both = 0;                     // matched vertices inside S_a ∩ S_b
-        for (int j = 0; j < da; ++j)
-            if (member(c, A, v[j]) && member(c, B, v[j])) ++both;
+        const unsigned ma = m & 0xffffu, mb = m >> 16;
+        const int a = A.n - __popc(ma), b = B.n - __popc(mb);
         acc.add((unsigned long long)a * (unsigned long long)b);
-        acc.sub((unsigned long long)(ab - both));
+        acc.sub((unsigned long long)(ab - __popc(ma & mb)));
     }
 }
 
@@ -1338,6 +1364,10 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
         }
     }
     if (cur_job >= 0) flush(acc, results + 2 * cur_job);
+    // busy cycles: from this warp's start to the moment it found no work
+    // left (the persistent loop's exit); summed over warps it measures the
+    // launch's total work, independent of how evenly the work spread
+    if (lane == 0) atomicAdd(stats + 2, (unsigned long long)(clock64() - t_start));
     if (kStats) {
         for (int o = 16; o; o >>= 1) my_bytes += __shfl_down_sync(kFull, my_bytes, o);
         if (lane == 0 && my_bytes) atomicAdd(stats, my_bytes);
@@ -1608,7 +1638,7 @@ gp_status scratch_bytes(const CountJob* jobs, int njobs, const LaunchOpts& opt, 
 
 gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& opt, cudaStream_t st,
                     uint64_t* results, int64_t* processed, float* kernel_ms, uint64_t* algo_bytes,
-                    int* aborted, uint64_t* algo_ops) {
+                    int* aborted, uint64_t* algo_ops, uint64_t* busy) {
     if (njobs <= 0) { set_error("no jobs"); return GP_ERR_ARG; }
     Geometry geo;
     gp_status grc = geometry(jobs, njobs, opt, &geo);
@@ -1624,9 +1654,9 @@ gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& opt, cuda
 
     // device buffers: job table, results (2 per job), cursor, error word
     const size_t jobs_b = sizeof(CountJob) * (size_t)njobs;
-    // results (2 per job), cursor, error word, stats (bytes, operations), then
-    // one abort flag per job
-    const size_t res_b = sizeof(unsigned long long) * (2 * (size_t)njobs + 4) + sizeof(int) * (size_t)njobs;
+    // results (2 per job), cursor, error word, stats (bytes, operations, busy
+    // warp cycles), then one abort flag per job
+    const size_t res_b = sizeof(unsigned long long) * (2 * (size_t)njobs + 5) + sizeof(int) * (size_t)njobs;
     void* d_mem = nullptr;
     int32_t* d_slots = nullptr;
     GP_CUDA_TRY(cudaMallocAsync(&d_mem, jobs_b + res_b + 64, st));
@@ -1641,7 +1671,7 @@ gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& opt, cuda
     unsigned long long* d_cursor = d_res + 2 * njobs;
     int* d_err = reinterpret_cast<int*>(d_cursor + 1);
     unsigned long long* d_stats = d_cursor + 2;
-    int* d_aborts = reinterpret_cast<int*>(d_stats + 2);
+    int* d_aborts = reinterpret_cast<int*>(d_stats + 3);
     gp_status rc = GP_OK;
     std::vector<unsigned long long> h_res((res_b + 7) / 8, 0);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -1685,8 +1715,9 @@ gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& opt, cuda
     for (int j = 0; j < 2 * njobs; ++j) results[j] = h_res[j];
     if (algo_bytes) *algo_bytes = h_res[2 * njobs + 2];
     if (algo_ops) *algo_ops = h_res[2 * njobs + 3];
+    if (busy) { busy[0] = h_res[2 * njobs + 4]; busy[1] = (uint64_t)blocks * kWarps; }
     if (aborted) {
-        const int* flags = reinterpret_cast<const int*>(h_res.data() + 2 * njobs + 4);
+        const int* flags = reinterpret_cast<const int*>(h_res.data() + 2 * njobs + 5);
         for (int j = 0; j < njobs; ++j) aborted[j] = flags[j];
     }
     int64_t done = (int64_t)std::min<unsigned long long>(h_res[2 * njobs], (unsigned long long)total);
@@ -1699,7 +1730,7 @@ gp_status run_count_in_scratch(const CountJob* jobs, int njobs, void* d_scratch,
     constexpr int kMaxJobs = 8;            // host result words live on the stack
     if (njobs <= 0 || njobs > kMaxJobs) { set_error("1 to %d jobs per call", kMaxJobs); return GP_ERR_ARG; }
     // layout: [result words | job table | intermediate sets], 256-byte aligned
-    const size_t words_b = ((sizeof(unsigned long long) * (2 * (size_t)njobs + 5)) + 255) & ~(size_t)255;
+    const size_t words_b = ((sizeof(unsigned long long) * (2 * (size_t)njobs + 6)) + 255) & ~(size_t)255;
     const size_t jobs_b = ((sizeof(CountJob) * (size_t)njobs) + 255) & ~(size_t)255;
     if (words_b + jobs_b > scratch_bytes) {
         set_error("%d jobs need %zu bytes of fixed scratch for results and job table; it holds %zu",
@@ -1733,7 +1764,7 @@ gp_status run_count_in_scratch(const CountJob* jobs, int njobs, void* d_scratch,
     unsigned long long* d_cursor = d_res + 2 * njobs;
     int* d_err = reinterpret_cast<int*>(d_cursor + 1);
     unsigned long long* d_stats = d_cursor + 2;
-    int* d_aborts = reinterpret_cast<int*>(d_stats + 2);       // unused: no cycle limit here
+    int* d_aborts = reinterpret_cast<int*>(d_stats + 3);       // unused: no cycle limit here
     CountJob* d_jobs = reinterpret_cast<CountJob*>(base + words_b);
     int32_t* d_slots = reinterpret_cast<int32_t*>(base + words_b + jobs_b);
     unsigned long long h_res[2 * kMaxJobs + 3] = {};

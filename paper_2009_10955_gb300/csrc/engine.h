@@ -95,10 +95,13 @@ struct LaunchOpts {
 // receive job j's 128-bit count (lo, hi). *processed receives how many
 // global tasks (from 0) were completed (< total only with a budget).
 // With lo.stats, *algo_bytes receives the list-path bytes and *algo_ops the
-// bitmap-subtree word operations of the launch.
+// bitmap-subtree word operations of the launch. busy (2 words) receives the
+// sum over warps of the cycles each spent before finding no work left, and
+// the number of warps launched.
 gp_status run_count(const CountJob* jobs, int njobs, const LaunchOpts& lo, cudaStream_t st,
                     uint64_t* results, int64_t* processed, float* kernel_ms = nullptr,
-                    uint64_t* algo_bytes = nullptr, int* aborted = nullptr, uint64_t* algo_ops = nullptr);
+                    uint64_t* algo_bytes = nullptr, int* aborted = nullptr, uint64_t* algo_ops = nullptr,
+                    uint64_t* busy = nullptr);
 
 // run_count without allocating: results, job table and intermediate sets all
 // live in the caller's device buffer d_scratch (256-byte aligned); the grid

@@ -43,3 +43,22 @@ def test_instrumented_counts_and_tallies(env, pname):
         assert o == 0
     c2, b2, o2 = stats(N, g, sc, N.GP_COUNT_NO_CORE)
     assert c2 == plain and o2 == 0 and b2 >= b
+
+
+def test_busy_cycles(env):
+    """Busy warp cycles: positive, the launched warps a multiple of 8 (whole
+    blocks), and a count over half of the tasks is busy for less than the
+    whole count (the same plan, the same grid)."""
+    N, g = env
+    sc = N.gp_schedule(N.gp_pattern_create(named_pattern("house")), g)
+    nnz = g.device_csr()[2]
+
+    def busy(**kw):
+        b = (ctypes.c_uint64 * 2)()
+        N.gp_count(g, sc, 0, N.make_opts(busy_cycles=ctypes.cast(b, ctypes.POINTER(ctypes.c_uint64)), **kw))
+        return b[0], b[1]
+
+    whole, warps = busy()
+    assert whole > 0 and warps > 0 and warps % 8 == 0
+    half, warps2 = busy(task_begin=nnz // 2)
+    assert warps2 == warps and 0 < half < whole
