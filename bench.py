@@ -71,7 +71,7 @@ def parse():
                     help="plain enumeration only (default: inclusion-exclusion for the innermost loops where a "
                          "plan qualifies, Section IV-D)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU-baseline sample budget")
-    ap.add_argument("--project-limit-s", type=float, default=60.0,
+    ap.add_argument("--project-limit-s", type=float, default=120.0,
                     help="patterns outside the step: the device budget of their whole count")
     ap.add_argument("--batched-graph", default="rmat20",
                     help="graph of the batched comparison (64 random patterns x top-3 plans; '' to skip)")
@@ -455,6 +455,8 @@ def gpu_arm(a, rank, world):
     def count(p, timed):
         """One timed count; returns the undivided total of this rank's tasks
         (the count for plain plans), the call's and the kernel's ms."""
+        if hi <= lo:                                       # an empty share (task_end 0 would mean all)
+            return 0, 0.0, 0.0
         flush.fill_(1)                                     # evict the graph from L2
         o = knobs(p, task_begin=lo, task_end=hi, kernel_ms=ctypes.pointer(ms),
                   raw_total=ctypes.cast(raw_buf, ctypes.POINTER(ctypes.c_uint64)))
@@ -939,7 +941,7 @@ def directed_bench(N, stream, scales=(14, 16, 18), reps=3):
             "timing": "wall time of the synchronous gp_dcount call (planning included), best of 3"}
 
 
-def model_bench(N, stream, graph_name, patterns, max_configs=120, limit_s=10.0, iep=False):
+def model_bench(N, stream, graph_name, patterns, max_configs=40, limit_s=5.0, iep=False):
     """Performance-model accuracy (the shape of the paper's Fig. 9, Fig. 10
     and Table II on a synthetic graph): every efficient schedule x
     restriction set (evenly subsampled beyond max_configs, the model's pick
@@ -967,7 +969,7 @@ def model_bench(N, stream, graph_name, patterns, max_configs=120, limit_s=10.0, 
             one = N.gp_schedule_explicit(p, sc, rs)
             if iep:
                 one.set_iep(True)
-            rec = timed_or_projected(N, g, one, stream, limit_s=limit_s)
+            rec = timed_or_projected(N, g, one, stream, limit_s=limit_s, sample_s=limit_s)
             if "count" in rec:
                 if count is None:
                     count = rec["count"]
@@ -993,7 +995,8 @@ def model_bench(N, stream, graph_name, patterns, max_configs=120, limit_s=10.0, 
                      "mean_set_vs_best_set_same_schedule": float(np.mean(same)) / min(same) if same else None})
         print(json.dumps(rows[-1], default=str), file=sys.stderr, flush=True)
     return {"metric": "performance-model accuracy", "graph": graph_name, "iep": iep,
-            "timing": f"whole counts below {limit_s} s, else projections from the same 256 x 64-task sample",
+            "timing": f"whole counts below {limit_s} s, else projections (busy warp cycles) from the same "
+                      "1024 x 64-task sample",
             "rows": rows}
 
 

@@ -302,8 +302,10 @@ typedef struct gp_count_opts {
 gp_status gp_count(gp_graph* g, const gp_schedules* s, int32_t idx, const gp_count_opts* opts,
                    void* stream, uint64_t* out);
 
-/* Count several (graph, schedule, plan) jobs in ONE persistent launch; work
- * items of all jobs share one device work queue. out[j] receives job j's
+/* Count several (graph, schedule, plan) jobs in one persistent launch per
+ * kernel build (jobs wanting the same register budget and inclusion-
+ * exclusion code share one; at most four builds exist); work items of the
+ * jobs of a launch share one device work queue. out[j] receives job j's
  * count. All graphs must live on the current device. With opts->raw_total
  * (2 x njobs words) each job's undivided 128-bit total is written there too,
  * and a count beyond 64 bits is not an error: its out[j] is 0 and the count

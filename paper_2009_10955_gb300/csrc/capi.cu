@@ -1,6 +1,7 @@
 // capi.cu -- the C ABI of libgraphpi_gb300.so (declared in include/graphpi.h).
 // Argument checking, handle management and host<->device marshalling; all
 // graph and counting work runs in the kernels of graph.cu and count.cu.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -635,7 +636,6 @@ gp_status gp_count_batch(gp_graph* const* graphs, const gp_schedules* const* sch
     gp_status rc = ensure_device(graphs[0]);
     if (rc != GP_OK) return rc;
     std::vector<uint64_t> res(2 * (size_t)njobs, 0);
-    int64_t done = 0;
     LaunchOpts lo = launch_opts(opts);
     lo.budget_cycles = 0;
     float ms = 0.f;
@@ -643,9 +643,44 @@ gp_status gp_count_batch(gp_graph* const* graphs, const gp_schedules* const* sch
     const bool want_ms = opts && opts->kernel_ms;
     std::vector<int> aborted((size_t)njobs, 0);
     uint64_t ops = 0, busy[2] = {0, 0};
-    rc = run_count(jobs.data(), njobs, lo, static_cast<cudaStream_t>(stream), res.data(), &done,
-                   want_ms ? &ms : nullptr, &bytes, aborted.data(), &ops, busy);
-    if (rc != GP_OK) return rc;
+    // one persistent launch per kernel build: jobs that want different
+    // register budgets (or the general inclusion-exclusion code) would
+    // otherwise all run with the build the most demanding one needs
+    std::vector<int> key((size_t)njobs);
+    for (int32_t j = 0; j < njobs; ++j) key[j] = kernel_variant(jobs[j], lo);
+    std::vector<int> keys(key);
+    std::sort(keys.begin(), keys.end());
+    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+    for (int kv : keys) {
+        std::vector<CountJob> group;
+        std::vector<int32_t> members;
+        int64_t goff = 0;
+        for (int32_t j = 0; j < njobs; ++j) {
+            if (key[j] != kv) continue;
+            group.push_back(jobs[j]);
+            group.back().task_offset = goff;
+            goff += jobs[j].nvirt;
+            members.push_back(j);
+        }
+        std::vector<uint64_t> gres(2 * group.size(), 0);
+        std::vector<int> gab(group.size(), 0);
+        int64_t done = 0;
+        float gms = 0.f;
+        uint64_t gbytes = 0, gops = 0, gbusy[2] = {0, 0};
+        rc = run_count(group.data(), (int)group.size(), lo, static_cast<cudaStream_t>(stream), gres.data(), &done,
+                       want_ms ? &gms : nullptr, &gbytes, gab.data(), &gops, gbusy);
+        if (rc != GP_OK) return rc;
+        for (size_t q = 0; q < members.size(); ++q) {
+            res[2 * members[q]] = gres[2 * q];
+            res[2 * members[q] + 1] = gres[2 * q + 1];
+            aborted[members[q]] = gab[q];
+        }
+        ms += gms;
+        bytes += gbytes;
+        ops += gops;
+        busy[0] += gbusy[0];
+        busy[1] = std::max(busy[1], gbusy[1]);
+    }
     for (int32_t j = 0; j < njobs; ++j)
         if (aborted[j]) return fail(GP_ERR_TIMEOUT, "a work item outlived opts.task_cycles; the batch was abandoned");
     if (want_ms) *opts->kernel_ms = ms;

@@ -466,11 +466,95 @@ __device__ __forceinline__ bool count_last_lane(const TaskCtx& c, const int* v, 
 // S_b (depth k-1), minus already-matched vertices, and must differ:
 // |S_a| |S_b| - |S_a ∩ S_b|. The plan has no restriction acting at those
 // depths; the host divides the job's total by the plan's iep_div.
+// Is x in list a? Binary search from position `from` (x is not below a.p[from]
+// when from > 0); *pos receives the search position for the next, larger x.
+__device__ __forceinline__ bool member_from(const TaskCtx& c, List a, int x, int from, int* pos) {
+    if (is_core(c, a.v) && x < c.core_n) { *pos = from; return core_bit(c, a.v, x); }
+    const int p = from + lower_bound(a.p + from, a.n - from, x);
+    *pos = p;
+    return p < a.n && __ldg(a.p + p) == x;
+}
+
+// The fused form (plan.iep_fuse): one inner set F = base ∩ N(v_{k-3}) is
+// never stored. One pass over the list choose() iterates counts |F| (the
+// elements found in the probed list) and |F ∩ O| (those also in the other
+// inner set O, searched with a window that narrows as the elements grow).
+// Returns both, warp-uniform.
+__device__ __forceinline__ int2 fused_counts(const TaskCtx& c, const Probe& q, List O) {
+    const int n = q.it.n, lane = c.lane;
+    int nf = 0, nfo = 0, from = q.bitmap ? q.tail : 0, from_o = 0;
+    for (int base = 0; base < n; base += 32) {
+        const int i = base + lane;
+        int x = INT_MAX, pos = q.pr.n, pos_o = 0;
+        bool f = false, searched = false;
+        if (i < n) {
+            x = __ldg(q.it.p + i);
+            if (q.bitmap && x < c.core_n) {
+                f = core_bit(c, q.pr.v, x);
+            } else {
+                pos = from + lower_bound(q.pr.p + from, q.pr.n - from, x);
+                f = pos < q.pr.n && __ldg(q.pr.p + pos) == x;
+                searched = true;
+            }
+        }
+        bool fo = false;
+        if (f) fo = member_from(c, O, x, from_o, &pos_o);
+        nf += __popc(__ballot_sync(kFull, f));
+        nfo += __popc(__ballot_sync(kFull, fo));
+        // later elements are larger: narrow both searched ranges
+        const int last = min(31, n - 1 - base);
+        const int lpos = __shfl_sync(kFull, pos, last);
+        if (__shfl_sync(kFull, (int)searched, last)) from = lpos;
+        // the next batch's elements exceed lx: O's searches start at lx's
+        // lower bound
+        const int lx = __shfl_sync(kFull, x, last);
+        int p0 = 0;
+        if (lane == 0) p0 = from_o + lower_bound(O.p + from_o, O.n - from_o, lx);
+        from_o = __shfl_sync(kFull, p0, 0);
+    }
+    if (c.sbytes && lane == 0) *c.sbytes += intersect_bytes(q.it.n, q.pr.n) + intersect_bytes(nf, O.n);
+    return make_int2(nf, nfo);
+}
+
 __device__ __forceinline__ void iep_count2(const TaskCtx& c, const int* v, Acc& acc) {
     const GpPlan& P = *c.P;
     const int da = P.k - 2, db = P.k - 1;
     const GpLevel& LA = P.lvl[da];
     const GpLevel& LB = P.lvl[db];
+    if (P.iep_fuse) {
+        const int dF = P.k - 3 + P.iep_fuse, dO = (dF == da) ? db : da;
+        const GpLevel& LF = P.lvl[dF];
+        const GpLevel& LO = P.lvl[dO];
+        const GpBuild& Bf = P.iep_build;
+        const List base = (Bf.base_kind == 1) ? nbr(c, v[Bf.base]) : slot(c, Bf.base);
+        const List nd = nbr(c, v[P.k - 3]);
+        const Window wf = window(Bf.lo_mask | LF.lo_mask, Bf.hi_mask | LF.hi_mask, v);
+        const Window wo = window(LO.lo_mask, LO.hi_mask, v);
+        const List O = clip((LO.src_kind == 1) ? nbr(c, v[LO.src]) : slot(c, LO.src), wo);
+        const Probe q = choose(c, base, nd, wf);
+        const int2 cnt = fused_counts(c, q, O);
+        // matched vertices in F (in the window, in base and in N(v_{k-3})),
+        // in O, and in both: lane j tests v_j for F, lane 16 + j for O
+        const int j = c.lane & 15;
+        const bool forF = c.lane < 16;
+        bool in = false;
+        if (j < da && ((forF ? LF.excl_mask : LO.excl_mask) >> j & 1)) {
+            const int x = v[j];
+            if (forF) {
+                in = x > wf.lo && x < wf.hi && member(c, base, x) && member(c, nd, x);
+            } else {
+                in = x > wo.lo && x < wo.hi && member(c, O, x);
+            }
+        }
+        const unsigned m = __ballot_sync(kFull, in);
+        if (c.lane == 0) {
+            const unsigned mf = m & 0xffffu, mo = m >> 16;
+            const int a = cnt.x - __popc(mf), b = O.n - __popc(mo);
+            acc.add((unsigned long long)a * (unsigned long long)b);
+            acc.sub((unsigned long long)(cnt.y - __popc(mf & mo)));
+        }
+        return;
+    }
     const Window wa = window(LA.lo_mask, LA.hi_mask, v), wb = window(LB.lo_mask, LB.hi_mask, v);
     const List A = clip((LA.src_kind == 1) ? nbr(c, v[LA.src]) : slot(c, LA.src), wa);
     const List B = clip((LB.src_kind == 1) ? nbr(c, v[LB.src]) : slot(c, LB.src), wb);
@@ -499,15 +583,6 @@ __device__ __forceinline__ void iep_count2(const TaskCtx& c, const int* v, Acc& 
         acc.add((unsigned long long)a * (unsigned long long)b);
         acc.sub((unsigned long long)(ab - __popc(ma & mb)));
     }
-}
-
-// Is x in list a? Binary search from position `from` (x is not below a.p[from]
-// when from > 0); *pos receives the search position for the next, larger x.
-__device__ __forceinline__ bool member_from(const TaskCtx& c, List a, int x, int from, int* pos) {
-    if (is_core(c, a.v) && x < c.core_n) { *pos = from; return core_bit(c, a.v, x); }
-    const int p = from + lower_bound(a.p + from, a.n - from, x);
-    *pos = p;
-    return p < a.n && __ldg(a.p + p) == x;
 }
 
 // Inclusion-exclusion for the last kk >= 3 depths (Section IV-D). With the
@@ -1627,6 +1702,18 @@ gp_status geometry(const CountJob* jobs, int njobs, const LaunchOpts& opt, Geome
 }
 
 }  // namespace
+
+int kernel_variant(const CountJob& job, const LaunchOpts& opt) {
+    // the variant key geometry() would pick for this job alone: general
+    // inclusion-exclusion, and the register budget of the default blocks
+    // per SM (3 for the three-level lane tail, else 4)
+    const GpPlan& P = job.plan;
+    int want = opt.blocks_per_sm > 0 ? opt.blocks_per_sm : 4;
+    if (opt.blocks_per_sm <= 0 && !opt.no_core && opt.bitmap_mode == 2 && P.core_dfs && job.core_bits && P.k >= 5 &&
+        P.lvl[P.k - 2].bm_inc && P.lvl[P.k - 1].bm_inc)
+        want = 3;
+    return (P.iep >= 3 ? 8 : 0) + want;
+}
 
 gp_status scratch_bytes(const CountJob* jobs, int njobs, const LaunchOpts& opt, uint64_t* bytes) {
     Geometry g;

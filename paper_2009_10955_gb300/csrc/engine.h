@@ -124,6 +124,11 @@ gp_status job_total(const CountJob& job, const uint64_t* res, uint64_t* out);
 gp_status run_list(const CountJob& job, int32_t* d_out, int64_t capacity, cudaStream_t st,
                    int64_t* n_written, int64_t* cut_tasks, int64_t* total = nullptr);
 
+// Key of the kernel build geometry() would pick for this job alone (its
+// register budget and whether it carries general inclusion-exclusion); jobs
+// with equal keys run best in one launch.
+int kernel_variant(const CountJob& job, const LaunchOpts& opt);
+
 // Device scratch run_count would allocate for these jobs and options.
 gp_status scratch_bytes(const CountJob* jobs, int njobs, const LaunchOpts& lo, uint64_t* bytes);
 

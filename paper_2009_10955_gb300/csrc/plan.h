@@ -69,4 +69,11 @@ struct GpPlan {
     int32_t labeled;
     int32_t label[GP_MAX_K];
     GpLevel lvl[GP_MAX_K];
+    // Two-loop inclusion-exclusion with one inner set never stored: that
+    // set (depth k-3 + iep_fuse, 1 or 2) is iep_build's intersection of the
+    // depth k-3 vertex's neighbours with its base, which no other level
+    // reads; its size and its intersection with the other inner set are
+    // counted in one pass (0: both inner sets are read from their lists).
+    int32_t iep_fuse;
+    GpBuild iep_build;
 };

@@ -460,6 +460,42 @@ bool iep_divisor(const PatternInfo& p, const int8_t* sched, ResMask res, int kk,
     return true;
 }
 
+namespace {
+
+// Two-loop inclusion-exclusion: when an inner set is a slot built at the
+// last outer depth and read by nothing but its inner level, drop that build
+// and let the kernel count the set (and its intersection with the other
+// inner set) in one pass instead of storing it.
+void fuse_inner_set(GpPlan* P) {
+    const int k = P->k, d = k - 3;
+    if (d < 1) return;
+    for (int which = 0; which < 2; ++which) {
+        const int x = k - 2 + which;
+        const GpLevel& L = P->lvl[x];
+        if (L.src_kind != 2) continue;
+        const int slot_id = L.src;
+        if (P->lvl[k - 2 + (1 - which)].src_kind == 2 && P->lvl[k - 2 + (1 - which)].src == slot_id) continue;
+        bool other_use = P->last_count_only && P->last_base_kind == 2 && P->last_base == slot_id;
+        for (int y = 0; y < k; ++y) {
+            if (y != x && P->lvl[y].src_kind == 2 && P->lvl[y].src == slot_id) other_use = true;
+            for (int q = 0; q < P->lvl[y].nbuild; ++q)
+                if (P->lvl[y].build[q].base_kind == 2 && P->lvl[y].build[q].base == slot_id) other_use = true;
+        }
+        if (other_use) continue;
+        GpLevel& B = P->lvl[d];
+        for (int q = 0; q < B.nbuild; ++q) {
+            if (B.build[q].dst != slot_id) continue;
+            P->iep_fuse = 1 + which;
+            P->iep_build = B.build[q];
+            for (int r = q + 1; r < B.nbuild; ++r) B.build[r - 1] = B.build[r];
+            --B.nbuild;
+            return;
+        }
+    }
+}
+
+}  // namespace
+
 int iep_depth(const PatternInfo& p, const int8_t* sched) {
     const int k = p.k;
     int kk = 1;                                 // trailing vertices pairwise non-adjacent
@@ -489,6 +525,7 @@ bool compile_plan_iep(const PatternInfo& p, const int8_t* sched, ResMask res, Gp
         // vertices inside an inner candidate set
         const uint8_t outer_mask = (uint8_t)((1u << (k - kk)) - 1u);
         for (int x = k - kk; x < k; ++x) out->lvl[x].excl_mask &= outer_mask;
+        if (kk == 2) fuse_inner_set(out);
         return true;
     }
     err = "inclusion-exclusion does not apply to this configuration";
