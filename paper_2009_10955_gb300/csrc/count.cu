@@ -1832,7 +1832,10 @@ gp_status geometry(const CountJob* jobs, int njobs, const LaunchOpts& opt, Geome
     g->smem = (size_t)kWarps * (size_t)g->bm_sets * (size_t)g->bm_stride * sizeof(uint32_t);
     if (pair_queue && !opt.stats && !general_iep && g->bm_stride > 0)
         g->smem += (size_t)kWarps * kPairQueue * sizeof(uint32_t);
-    if (g->smem > 48 * 1024)
+    // static and dynamic shared memory together may pass the 48 KB a block
+    // gets without opting in (seven-vertex cliques on a full core: 48 KB of
+    // bitmaps alone), so opt in for whatever dynamic size the launch uses
+    if (g->smem > 0)
         GP_CUDA_TRY(cudaFuncSetAttribute(g->kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem));
     GP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, g->kern, kWarps * 32, g->smem));
     int per_sm = std::min(want, occ);

@@ -468,3 +468,17 @@ def test_chung_lu_4m_whole_k6e_agrees_across_plans_and_paths(N):
     si = N.gp_schedule(N.gp_pattern_create(adj), g)
     assert si.set_iep(True) == 1
     assert N.gp_count(g, si, 0) == base
+
+
+@pytest.mark.parametrize("pname", ["k6", "k7"])
+def test_large_cliques_on_a_full_core(N, pname):
+    """Six- and seven-vertex cliques on a graph whose core bit matrix is full
+    (8,192 vertices, 256 words a row): the bitmap subtree then needs 40 and
+    48 KB of shared memory per block, beside the kernel's own; every bitmap
+    variant must launch and equal the list path."""
+    g, _ = graph_pair(N, "rmat14")
+    s = N.gp_schedule(N.gp_pattern_create(named_pattern(pname)), g)
+    lists = N.gp_count(g, s, 0, N.make_opts(flags=N.GP_COUNT_NO_CORE))
+    assert lists[0] == N.GP_OK
+    for f in (0, N.GP_COUNT_WARP_BITMAP, N.GP_COUNT_LANE_BITMAP, N.GP_COUNT_PAIR_QUEUE):
+        assert N.gp_count(g, s, 0, N.make_opts(flags=f)) == lists, f
