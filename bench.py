@@ -809,17 +809,10 @@ def serve_bench(N, stream, scales, rates, per_rate, deadline_s, slice_ms, mem_bu
 
 
 def sample_windows(nnz, windows, width, seed):
-    """Stratified task windows: one window of `width` tasks at a seeded
-    random offset inside each of `windows` equal slices of the task space."""
-    rng = np.random.default_rng(seed)
-    if nnz <= windows * width:
-        return [(0, nnz)]
-    stride = nnz // windows
-    out = []
-    for i in range(windows):
-        b = i * stride + int(rng.integers(0, max(1, stride - width)))
-        out.append((b, min(nnz, b + width)))
-    return out
+    """Stratified task windows (one per equal slice of the task space, at a
+    seeded offset): the autotuner's sampler."""
+    from paper_2009_10955_gb300.autotune import sample_ranges
+    return sample_ranges(nnz, windows, width, seed)
 
 
 def budgeted_count(N, g, s, stream, limit_s):

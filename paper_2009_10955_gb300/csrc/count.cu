@@ -252,7 +252,7 @@ __device__ __forceinline__ int warp_merge(const TaskCtx& c, const int32_t* __res
         for (int st = 16; st; st >>= 1)
             if (__shfl_sync(kFull, y, pos + st - 1) < x) pos += st;
         const int yp = __shfl_sync(kFull, y, pos);        // every lane takes part
-        const bool mine = ia + lane < na && x <= bmax;   // resolved in this round
+        const bool mine = ia + lane < na && x <= bmax;   // resolved by this tile pair
         const bool f = mine && yp == x;
         const unsigned m = __ballot_sync(kFull, f);
         if (out && f) {
@@ -1832,10 +1832,13 @@ gp_status geometry(const CountJob* jobs, int njobs, const LaunchOpts& opt, Geome
     g->smem = (size_t)kWarps * (size_t)g->bm_sets * (size_t)g->bm_stride * sizeof(uint32_t);
     if (pair_queue && !opt.stats && !general_iep && g->bm_stride > 0)
         g->smem += (size_t)kWarps * kPairQueue * sizeof(uint32_t);
-    // static and dynamic shared memory together may pass the 48 KB a block
-    // gets without opting in (seven-vertex cliques on a full core: 48 KB of
-    // bitmaps alone), so opt in for whatever dynamic size the launch uses
-    if (g->smem > 0)
+    // opt in beyond the 48 KB a block gets by default only when static and
+    // dynamic shared memory together need it (seven-vertex cliques on a full
+    // core: 48 KB of bitmaps alone); raising the limit for every launch moved
+    // the shared-memory/L1 split and slowed L1-bound counts
+    cudaFuncAttributes fa;
+    GP_CUDA_TRY(cudaFuncGetAttributes(&fa, g->kern));
+    if (g->smem + fa.sharedSizeBytes > 48 * 1024)
         GP_CUDA_TRY(cudaFuncSetAttribute(g->kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem));
     GP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, g->kern, kWarps * 32, g->smem));
     int per_sm = std::min(want, occ);
