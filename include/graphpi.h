@@ -290,10 +290,6 @@ typedef struct gp_count_opts {
 #define GP_COUNT_LANE_BITMAP 8 /* bitmap subtree: one candidate per lane for the
                               last two levels only (GP_COUNT_WARP_BITMAP wins
                               when both are set)                                  */
-#define GP_COUNT_PAIR_QUEUE 16 /* bitmap subtree, last three levels: the lanes
-                              queue their (depth k-3, depth k-2) candidate
-                              pairs in shared memory and count them one pair
-                              per lane (the two flags above win when set)         */
 
 /* Count the embeddings of the pattern of `s` in `g` with plan `idx`.
  * Every embedding is counted exactly once (restrictions, Algorithm 1).

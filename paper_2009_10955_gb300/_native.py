@@ -31,7 +31,6 @@ GP_COUNT_STATS = 1
 GP_COUNT_NO_CORE = 2
 GP_COUNT_WARP_BITMAP = 4
 GP_COUNT_LANE_BITMAP = 8
-GP_COUNT_PAIR_QUEUE = 16
 
 # Every function the header declares, with its ctypes signature.
 P = ctypes.c_void_p

@@ -184,7 +184,6 @@ LaunchOpts launch_opts(const gp_count_opts* o) {
         if (o->task_cycles > 0) lo.task_cycles = o->task_cycles;
         if (o->flags & GP_COUNT_WARP_BITMAP) lo.bitmap_mode = 0;
         else if (o->flags & GP_COUNT_LANE_BITMAP) lo.bitmap_mode = 1;
-        else if (o->flags & GP_COUNT_PAIR_QUEUE) lo.bitmap_mode = 3;
         if (o->lane_work > 0) lo.lane_work = o->lane_work;
     }
     return lo;

@@ -114,7 +114,6 @@ struct TaskCtx {
     int bm_stride;         // words per bitmap set
     bool lane_bitmap;      // bitmap last level: one candidate per lane
     bool lane_three;       // bitmap last three levels: one candidate per lane where the plan allows
-    uint32_t* pq;          // pair queue of the last three levels (shared memory, per warp) or null
     int lane;
     int lane_work;         // per-lane work limit before handing to the warp
     int* err;
@@ -1133,141 +1132,6 @@ __device__ __forceinline__ void bitmap_last_three(const TaskCtx& c, int* v, int 
     acc.add(mine);
 }
 
-// Entries of the per-warp pair queue of bitmap_last_three_queued.
-constexpr int kPairQueue = 256;
-
-// bitmap_last_three with the pairs balanced over the lanes: each lane walks
-// its candidate x's set S_{k-3} AND row(x) (level k-2's window) one member y
-// per step and appends (x, y) to a per-warp queue in shared memory; when the
-// queue fills, the warp counts the queued pairs one per lane (the last
-// level's set S_{k-3} AND row(x) AND row(y) inside its window). A lane whose
-// candidate has many members no longer keeps the others waiting.
-__device__ __forceinline__ void bitmap_last_three_queued(const TaskCtx& c, int* v, int Ws, Acc& acc, int part,
-                                                         int nparts) {
-    const GpPlan& P = *c.P;
-    const int d = P.k - 3, e = P.k - 2;
-    const GpLevel& le = P.lvl[e];
-    const GpLevel& lL = P.lvl[P.k - 1];
-    const uint32_t* S = c.bm + (size_t)d * c.bm_stride;
-    const uint8_t xb = (uint8_t)(1u << d), yb = (uint8_t)(1u << e);
-    const Window be = window(le.lo_mask & (uint8_t)~xb, le.hi_mask & (uint8_t)~xb, v);
-    const Window bL = window(lL.lo_mask & (uint8_t)~(xb | yb), lL.hi_mask & (uint8_t)~(xb | yb), v);
-    const bool e_xlo = le.lo_mask & xb, e_xhi = le.hi_mask & xb;
-    const bool L_xlo = lL.lo_mask & xb, L_xhi = lL.hi_mask & xb;
-    const bool L_ylo = lL.lo_mask & yb, L_yhi = lL.hi_mask & yb;
-    const uint8_t below = (uint8_t)((1u << d) - 1u);
-    const uint8_t ex_e = le.excl_mask & below, ex_L = (uint8_t)((le.excl_mask | lL.excl_mask) & below);
-    const RankScan rs = rank_scan(c, S, Ws);
-    const int np = (d == 2) ? nparts : 1, pt = (d == 2) ? part : 0;
-    const int J = (rs.T > pt) ? (rs.T - pt + np - 1) / np : 0;
-    const uint4* S4 = reinterpret_cast<const uint4*>(S);
-    uint32_t* Q = c.pq;
-    unsigned long long mine = 0;
-    // count the first qn queued pairs, one per lane
-    auto drain = [&](int qn) {
-        __syncwarp();
-        for (int p0 = 0; p0 < qn; p0 += 32) {
-            const int p = p0 + c.lane;
-            if (p >= qn) continue;
-            const uint32_t ent = Q[p];
-            const int x = (int)(ent >> 16), y = (int)(ent & 0xffffu);
-            int lo = bL.lo, hi = bL.hi;
-            if (L_xlo) lo = max(lo, x);
-            if (L_ylo) lo = max(lo, y);
-            if (L_xhi) hi = min(hi, x);
-            if (L_yhi) hi = min(hi, y);
-            const int w0 = max(0, (lo + 1) >> 5);
-            const int w1 = min(Ws, (hi == INT_MAX) ? Ws : ((hi + 31) >> 5));
-            const uint32_t* rx = c.core_bits + (size_t)x * c.core_words;
-            const uint32_t* ry = c.core_bits + (size_t)y * c.core_words;
-            const uint4* rx4 = reinterpret_cast<const uint4*>(rx);
-            const uint4* ry4 = reinterpret_cast<const uint4*>(ry);
-            int cnt = 0;
-            if (w0 < w1) {
-                const uint32_t m_first = window_bits(w0, lo, hi), m_last = window_bits(w1 - 1, lo, hi);
-                const int q0 = w0 >> 2, q1 = (w1 - 1) >> 2;
-                for (int q = q0; q <= q1; ++q) {
-                    const uint4 a = S4[q], b = __ldg(rx4 + q), f = __ldg(ry4 + q);
-                    uint32_t t4[4] = {a.x & b.x & f.x, a.y & b.y & f.y, a.z & b.z & f.z, a.w & b.w & f.w};
-                    if (q == q0 || q == q1) {
-#pragma unroll
-                        for (int t = 0; t < 4; ++t) {
-                            const int ww = 4 * q + t;
-                            uint32_t keep = (ww < w0 || ww >= w1) ? 0u : ~0u;
-                            if (ww == w0) keep &= m_first;
-                            if (ww == w1 - 1) keep &= m_last;
-                            t4[t] &= keep;
-                        }
-                    }
-                    cnt += __popc(t4[0]) + __popc(t4[1]) + __popc(t4[2]) + __popc(t4[3]);
-                }
-                if (c.sops) *c.sops += 3ull * (unsigned long long)(w1 - w0);
-            }
-            if (c.sops) *c.sops += 1;
-            if (ex_L) {
-                for (int jj = 0; jj < d; ++jj) {
-                    if (!((ex_L >> jj) & 1)) continue;
-                    const int u = v[jj];
-                    if (u <= lo || u >= hi || u >= 32 * Ws) continue;
-                    const int uw = u >> 5;
-                    cnt -= (int)((S[uw] & __ldg(rx + uw) & __ldg(ry + uw)) >> (u & 31) & 1u);
-                }
-            }
-            mine += (unsigned)cnt;
-        }
-        __syncwarp();
-    };
-    for (int j0 = 0; j0 < J; j0 += 32) {
-        if (over(c)) return;
-        const int j = j0 + c.lane;
-        const int x = rank_select(S, rs, pt + np * min(j, J - 1));
-        // this lane's walk: words [w, we1) of S AND row(x) inside level e's window
-        int w = 0, we1 = 0;
-        uint32_t m = 0;
-        int lo_e = -1, hi_e = INT_MAX;
-        const uint32_t* rx = c.core_bits + (size_t)x * c.core_words;
-        if (j < J) {
-            lo_e = e_xlo ? max(be.lo, x) : be.lo;
-            hi_e = e_xhi ? min(be.hi, x) : be.hi;
-            w = max(0, (lo_e + 1) >> 5);
-            we1 = min(Ws, (hi_e == INT_MAX) ? Ws : ((hi_e + 31) >> 5));
-            if (c.sops && we1 > w) *c.sops += (unsigned long long)(we1 - w);
-            if (w < we1) m = S[w] & __ldg(rx + w) & window_bits(w, lo_e, hi_e);
-        }
-        int qn = 0;
-        for (;;) {
-            // this lane's next member y (or none left)
-            int y = -1;
-            while (m == 0 && w + 1 < we1) {
-                ++w;
-                m = S[w] & __ldg(rx + w);
-                if (w == we1 - 1) m &= window_bits(w, lo_e, hi_e);
-            }
-            if (m) {
-                y = 32 * w + __ffs(m) - 1;
-                m &= m - 1;
-                if (ex_e)
-                    for (int jj = 0; jj < d; ++jj)
-                        if (((ex_e >> jj) & 1) && v[jj] == y) y = -1;
-            }
-            const bool more = m != 0 || w + 1 < we1;
-            const unsigned b = __ballot_sync(kFull, y >= 0);
-            if (y >= 0) Q[qn + __popc(b & lanemask_lt())] = ((uint32_t)x << 16) | (uint32_t)y;
-            qn += __popc(b);
-            const bool any_more = __any_sync(kFull, more);
-            if (qn > kPairQueue - 32 || (!any_more && qn > 0)) {
-                drain(qn);
-                qn = 0;
-            }
-            if (!any_more) break;
-        }
-    }
-    acc.add(mine);
-}
-
-// kPQ: the launch's build queues the pairs of the last three levels (only
-// the build launched for GP_COUNT_PAIR_QUEUE carries that code).
-template <bool kPQ>
 __device__ void bitmap_task(const TaskCtx& c, int* v, Acc& acc, int part, int nparts) {
     const GpPlan& P = *c.P;
     const int k = P.k;
@@ -1298,8 +1162,7 @@ __device__ void bitmap_task(const TaskCtx& c, int* v, Acc& acc, int part, int np
     int d = 2, ordinal2 = 0;
     Wd[2] = bitmap_build(c, v, 2, W, W, n0_smem);
     if (three && k == 5) {
-        if (kPQ && c.pq) bitmap_last_three_queued(c, v, Wd[2], acc, part, nparts);
-        else bitmap_last_three(c, v, Wd[2], acc, part, nparts);
+        bitmap_last_three(c, v, Wd[2], acc, part, nparts);
         return;
     }
     word[2] = -1;
@@ -1313,8 +1176,7 @@ __device__ void bitmap_task(const TaskCtx& c, int* v, Acc& acc, int part, int np
         v[d] = x;
         Wd[d + 1] = bitmap_build(c, v, d + 1, W, Wd[d], n0_smem);
         if (three && d + 1 == k - 3) {
-            if (kPQ && c.pq) bitmap_last_three_queued(c, v, Wd[d + 1], acc, 0, 1);
-            else bitmap_last_three(c, v, Wd[d + 1], acc, 0, 1);
+            bitmap_last_three(c, v, Wd[d + 1], acc, 0, 1);
         } else if (d + 1 == k - 2) {
             bitmap_last_two(c, v, W, Wd[d + 1], n0_smem, acc, 0, 1);
         } else {
@@ -1327,7 +1189,7 @@ __device__ void bitmap_task(const TaskCtx& c, int* v, Acc& acc, int part, int np
 
 // Remaining loops of one edge task (v0, v1), or of part `part` of `nparts`
 // of it: the parts share out the candidates of depth 2.
-template <bool kGeneralIep, bool kPQ>
+template <bool kGeneralIep>
 __device__ void run_task(const TaskCtx& c, int v0, int v1, Acc& acc, int part, int nparts) {
     const GpPlan& P = *c.P;
     const int k = P.k;
@@ -1344,7 +1206,7 @@ __device__ void run_task(const TaskCtx& c, int v0, int v1, Acc& acc, int part, i
     for (int i = 0; i < GP_MAX_K; ++i) v[i] = -1;
     v[0] = v0;
     v[1] = v1;
-    if (P.core_dfs && c.bm && v1 < c.core_n) { bitmap_task<kPQ>(c, v, acc, part, nparts); return; }
+    if (P.core_dfs && c.bm && v1 < c.core_n) { bitmap_task(c, v, acc, part, nparts); return; }
     const int d_iep = P.iep ? k - 1 - P.iep : -1;   // last outer depth of an inclusion-exclusion plan
     if (k == 3 || d_iep == 1) {
         if (part != 0) return;                 // no depth-2 loop to share out
@@ -1391,7 +1253,7 @@ __device__ void run_task(const TaskCtx& c, int v0, int v1, Acc& acc, int part, i
     }
 }
 
-template <bool kStats, int kMinBlocks, bool kGeneralIep, bool kPQ>
+template <bool kStats, int kMinBlocks, bool kGeneralIep>
 __global__ void __launch_bounds__(kWarps * 32, kMinBlocks)
 k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
         unsigned long long* __restrict__ cursor, unsigned long long* __restrict__ results,
@@ -1418,12 +1280,8 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
     c.deadline = &s_deadline[w];
     c.labels = nullptr;
     c.lane_bitmap = lane_bitmap != 0;
-    c.lane_three = lane_bitmap >= 2;
-    // 0 warp, 1 lane (last two levels), 2 lane (last three where allowed),
-    // 3 as 2 with the pairs of the last three levels queued over the lanes
-    const int bitmap_mode = lane_bitmap;
-    c.pq = (kPQ && bitmap_mode == 3 && bm_stride > 0)
-               ? s_bitmaps + (size_t)kWarps * bm_sets * bm_stride + (size_t)w * kPairQueue : nullptr;
+    c.lane_three = lane_bitmap == 2;
+    const int bitmap_mode = lane_bitmap;    // 0 warp, 1 lane (last two levels), 2 lane (last three where allowed)
     c.task_cycles = task_cycles;
     c.job_abort = aborts;
     if (lane == 0) s_deadline[w] = 0;
@@ -1493,7 +1351,7 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
                 // bitmap subtree: one candidate per lane (mode 1 or 2), and
                 // in mode 2 the three-level lane tail where the plan allows
                 c.lane_bitmap = bitmap_mode != 0;
-                c.lane_three = bitmap_mode >= 2;
+                c.lane_three = bitmap_mode == 2;
                 if (c.core_n == 0 || J.core_words > c.bm_stride) c.bm = nullptr;
                 else if (bm_stride > 0 && J.plan.k - 1 <= bm_sets)
                     c.bm = s_bitmaps + (size_t)w * bm_sets * bm_stride;
@@ -1519,7 +1377,7 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
                 const int hv1 = __ldg(c.col + eh);
                 if (lo1s && !(hv1 > rl)) continue;
                 if (hi1s && !(hv1 < rl)) continue;
-                run_task<kGeneralIep, kPQ>(c, rl, hv1, acc, part, job_split);
+                run_task<kGeneralIep>(c, rl, hv1, acc, part, job_split);
             }
             if (lt >= lt_end) { t = tend; continue; }
             int64_t e = job_begin + job_heavy + (lt - hp);
@@ -1574,7 +1432,7 @@ k_count(const CountJob* __restrict__ jobs, int njobs, int64_t total,
                     const int v1 = __ldg(c.col + e);
                     if (lo1 && !(v1 > v0)) continue;
                     if (hi1 && !(v1 < v0)) continue;
-                    run_task<kGeneralIep, kPQ>(c, v0, v1, acc, 0, 1);
+                    run_task<kGeneralIep>(c, v0, v1, acc, 0, 1);
                 }
             }
             t = tend;
@@ -1673,7 +1531,6 @@ k_list(const CountJob* __restrict__ job, int64_t ntasks, unsigned long long* __r
     c.bm_stride = 0;
     c.lane_bitmap = false;
     c.lane_three = false;
-    c.pq = nullptr;
     c.lane = lane;
     c.lane_work = kLaneWork;
     c.err = err;
@@ -1799,7 +1656,7 @@ gp_status geometry(const CountJob* jobs, int njobs, const LaunchOpts& opt, Geome
     int want = opt.blocks_per_sm;
     if (want <= 0) {
         want = 4;
-        if (!opt.no_core && opt.bitmap_mode >= 2)
+        if (!opt.no_core && opt.bitmap_mode == 2)
             for (int j = 0; j < njobs; ++j) {
                 const GpPlan& P = jobs[j].plan;
                 if (P.core_dfs && jobs[j].core_bits && P.k >= 5 && P.lvl[P.k - 2].bm_inc && P.lvl[P.k - 1].bm_inc)
@@ -1808,17 +1665,14 @@ gp_status geometry(const CountJob* jobs, int njobs, const LaunchOpts& opt, Geome
     }
     bool general_iep = false;              // some job replaces three or more loops
     for (int j = 0; j < njobs; ++j) general_iep |= jobs[j].plan.iep >= 3;
-    const bool pair_queue = opt.bitmap_mode == 3;
     if (opt.stats) {
-        g->kern = (want == 1 || want == 2) ? k_count<true, 1, true, false>
-                : (want == 3) ? k_count<true, 3, true, false> : k_count<true, 4, true, false>;
+        g->kern = (want == 1 || want == 2) ? k_count<true, 1, true>
+                : (want == 3) ? k_count<true, 3, true> : k_count<true, 4, true>;
     } else if (general_iep) {
-        g->kern = k_count<false, 4, true, false>;
-    } else if (pair_queue) {
-        g->kern = k_count<false, 3, false, true>;
+        g->kern = k_count<false, 4, true>;
     } else {
-        g->kern = (want == 1 || want == 2) ? k_count<false, 1, false, false>
-                : (want == 3) ? k_count<false, 3, false, false> : k_count<false, 4, false, false>;
+        g->kern = (want == 1 || want == 2) ? k_count<false, 1, false>
+                : (want == 3) ? k_count<false, 3, false> : k_count<false, 4, false>;
     }
     // bitmap sets in shared memory when some job may search a core subtree
     g->bm_stride = 0;
@@ -1830,8 +1684,6 @@ gp_status geometry(const CountJob* jobs, int njobs, const LaunchOpts& opt, Geome
                 g->bm_sets = std::max(g->bm_sets, jobs[j].plan.k - 1);
             }
     g->smem = (size_t)kWarps * (size_t)g->bm_sets * (size_t)g->bm_stride * sizeof(uint32_t);
-    if (pair_queue && !opt.stats && !general_iep && g->bm_stride > 0)
-        g->smem += (size_t)kWarps * kPairQueue * sizeof(uint32_t);
     // opt in beyond the 48 KB a block gets by default only when static and
     // dynamic shared memory together need it (seven-vertex cliques on a full
     // core: 48 KB of bitmaps alone); raising the limit for every launch moved
@@ -1863,7 +1715,7 @@ int kernel_variant(const CountJob& job, const LaunchOpts& opt) {
     // per SM (3 for the three-level lane tail, else 4)
     const GpPlan& P = job.plan;
     int want = opt.blocks_per_sm > 0 ? opt.blocks_per_sm : 4;
-    if (opt.blocks_per_sm <= 0 && !opt.no_core && opt.bitmap_mode >= 2 && P.core_dfs && job.core_bits && P.k >= 5 &&
+    if (opt.blocks_per_sm <= 0 && !opt.no_core && opt.bitmap_mode == 2 && P.core_dfs && job.core_bits && P.k >= 5 &&
         P.lvl[P.k - 2].bm_inc && P.lvl[P.k - 1].bm_inc)
         want = 3;
     return (P.iep >= 3 ? 8 : 0) + want;
@@ -1995,7 +1847,7 @@ gp_status run_count_in_scratch(const CountJob* jobs, int njobs, void* d_scratch,
     GP_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     bool general_iep = false;
     for (int j = 0; j < njobs; ++j) general_iep |= jobs[j].plan.iep >= 3;
-    auto kern = general_iep ? k_count<false, 4, true, false> : k_count<false, 4, false, false>;
+    auto kern = general_iep ? k_count<false, 4, true> : k_count<false, 4, false>;
     GP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWarps * 32, 0));
     int64_t blocks = std::min<int64_t>((int64_t)nsm * std::max(occ, 1), (int64_t)(slot_b / per_block));
     int64_t per_warp = total / (blocks * kWarps * 64);

@@ -87,7 +87,7 @@ struct LaunchOpts {
     bool stats = false;      // instrumented kernel that tallies algorithmic bytes and operations
     bool no_core = false;    // binary searches only (no core bit matrix)
     int64_t task_cycles = 0; // per-work-item cycle limit (0 = none)
-    int bitmap_mode = 2;     // bitmap subtree: 0 warp per candidate, 1 lane per candidate (last two levels), 2 (default) also the lane three-level tail, 3 that tail with its pairs queued over the lanes
+    int bitmap_mode = 2;     // bitmap subtree: 0 warp per candidate, 1 lane per candidate (last two levels), 2 (default) also the lane three-level tail
     int lane_work = 0;       // 0 = default
 };
 

@@ -155,7 +155,6 @@ def test_bitmap_paths_equal_list_path(N, gname, pname):
         assert N.gp_count(g, one) == lists, (sc, r)
         assert N.gp_count(g, one, 0, N.make_opts(flags=N.GP_COUNT_WARP_BITMAP)) == lists, (sc, r)
         assert N.gp_count(g, one, 0, N.make_opts(flags=N.GP_COUNT_LANE_BITMAP)) == lists, (sc, r)
-        assert N.gp_count(g, one, 0, N.make_opts(flags=N.GP_COUNT_PAIR_QUEUE)) == lists, (sc, r)
         if expect is None:
             expect = lists
         assert lists == expect, (sc, r)
@@ -207,7 +206,7 @@ def test_partial_core_graph(N, pname):
     for split in (2, 8, 33):           # high-degree tasks cut into parts
         assert N.gp_count(g, s, 0, N.make_opts(split=split)) == got
         assert N.gp_count(g, s, 0, N.make_opts(split=split, flags=N.GP_COUNT_NO_CORE)) == got
-        for f in (N.GP_COUNT_LANE_BITMAP, N.GP_COUNT_WARP_BITMAP, N.GP_COUNT_PAIR_QUEUE):
+        for f in (N.GP_COUNT_LANE_BITMAP, N.GP_COUNT_WARP_BITMAP):
             assert N.gp_count(g, s, 0, N.make_opts(split=split, flags=f)) == got
     if pname != "k5":
         assert got[1] == oracle.count_restricted(adj, order, res, ref)
@@ -447,7 +446,7 @@ def test_rmat20_whole_counts_agree_across_plans_and_paths(N, pname):
     assert base[0] == N.GP_OK and base[1] > 0
     for i in range(1, len(s)):
         assert N.gp_count(g, s, i) == base, i
-    for f in (N.GP_COUNT_NO_CORE, N.GP_COUNT_WARP_BITMAP, N.GP_COUNT_LANE_BITMAP, N.GP_COUNT_PAIR_QUEUE):
+    for f in (N.GP_COUNT_NO_CORE, N.GP_COUNT_WARP_BITMAP, N.GP_COUNT_LANE_BITMAP):
         assert N.gp_count(g, s, 0, N.make_opts(flags=f)) == base, f
     assert N.gp_count(g, s, 0, N.make_opts(split=8)) == base
 
@@ -480,5 +479,5 @@ def test_large_cliques_on_a_full_core(N, pname):
     s = N.gp_schedule(N.gp_pattern_create(named_pattern(pname)), g)
     lists = N.gp_count(g, s, 0, N.make_opts(flags=N.GP_COUNT_NO_CORE))
     assert lists[0] == N.GP_OK
-    for f in (0, N.GP_COUNT_WARP_BITMAP, N.GP_COUNT_LANE_BITMAP, N.GP_COUNT_PAIR_QUEUE):
+    for f in (0, N.GP_COUNT_WARP_BITMAP, N.GP_COUNT_LANE_BITMAP):
         assert N.gp_count(g, s, 0, N.make_opts(flags=f)) == lists, f
