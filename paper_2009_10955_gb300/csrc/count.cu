@@ -516,12 +516,15 @@ __device__ __forceinline__ int2 fused_counts(const TaskCtx& c, const Probe& q, L
     return make_int2(nf, nfo);
 }
 
+// kFused: the launch's build carries the fused form (the general
+// inclusion-exclusion build); other builds never see a fused plan.
+template <bool kFused>
 __device__ __forceinline__ void iep_count2(const TaskCtx& c, const int* v, Acc& acc) {
     const GpPlan& P = *c.P;
     const int da = P.k - 2, db = P.k - 1;
     const GpLevel& LA = P.lvl[da];
     const GpLevel& LB = P.lvl[db];
-    if (P.iep_fuse) {
+    if (kFused && P.iep_fuse) {
         const int dF = P.k - 3 + P.iep_fuse, dO = (dF == da) ? db : da;
         const GpLevel& LF = P.lvl[dF];
         const GpLevel& LO = P.lvl[dO];
@@ -712,11 +715,11 @@ __device__ __noinline__ void iep_count_sets(const TaskCtx& c, const int* v, Acc&
     }
 }
 
-// kGeneralIep: the launch may hold plans with kk >= 3 (kernels launched
-// without such plans carry no call to iep_count_sets).
+// kGeneralIep: the launch may hold plans with kk >= 3 or a fused two-loop
+// form (kernels launched without such plans carry none of that code).
 template <bool kGeneralIep>
 __device__ __forceinline__ void iep_count(const TaskCtx& c, const int* v, Acc& acc) {
-    if (!kGeneralIep || c.P->iep == 2) iep_count2(c, v, acc);
+    if (!kGeneralIep || c.P->iep == 2) iep_count2<kGeneralIep>(c, v, acc);
     else iep_count_sets(c, v, acc);
 }
 
@@ -1663,8 +1666,8 @@ gp_status geometry(const CountJob* jobs, int njobs, const LaunchOpts& opt, Geome
                     want = 3;
             }
     }
-    bool general_iep = false;              // some job replaces three or more loops
-    for (int j = 0; j < njobs; ++j) general_iep |= jobs[j].plan.iep >= 3;
+    bool general_iep = false;              // some job replaces three or more loops or fuses two
+    for (int j = 0; j < njobs; ++j) general_iep |= jobs[j].plan.iep >= 3 || jobs[j].plan.iep_fuse;
     if (opt.stats) {
         g->kern = (want == 1 || want == 2) ? k_count<true, 1, true>
                 : (want == 3) ? k_count<true, 3, true> : k_count<true, 4, true>;
@@ -1718,7 +1721,7 @@ int kernel_variant(const CountJob& job, const LaunchOpts& opt) {
     if (opt.blocks_per_sm <= 0 && !opt.no_core && opt.bitmap_mode == 2 && P.core_dfs && job.core_bits && P.k >= 5 &&
         P.lvl[P.k - 2].bm_inc && P.lvl[P.k - 1].bm_inc)
         want = 3;
-    return (P.iep >= 3 ? 8 : 0) + want;
+    return (P.iep >= 3 || P.iep_fuse ? 8 : 0) + want;
 }
 
 gp_status scratch_bytes(const CountJob* jobs, int njobs, const LaunchOpts& opt, uint64_t* bytes) {
@@ -1846,7 +1849,7 @@ gp_status run_count_in_scratch(const CountJob* jobs, int njobs, void* d_scratch,
     GP_CUDA_TRY(cudaGetDevice(&dev));
     GP_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     bool general_iep = false;
-    for (int j = 0; j < njobs; ++j) general_iep |= jobs[j].plan.iep >= 3;
+    for (int j = 0; j < njobs; ++j) general_iep |= jobs[j].plan.iep >= 3 || jobs[j].plan.iep_fuse;
     auto kern = general_iep ? k_count<false, 4, true> : k_count<false, 4, false>;
     GP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWarps * 32, 0));
     int64_t blocks = std::min<int64_t>((int64_t)nsm * std::max(occ, 1), (int64_t)(slot_b / per_block));
