@@ -651,17 +651,28 @@ gp_status gp_count_batch(gp_graph* const* graphs, const gp_schedules* const* sch
     std::vector<int> keys(key);
     std::sort(keys.begin(), keys.end());
     keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+    int nsm = 0, dev = 0;
+    GP_CUDA_TRY(cudaGetDevice(&dev));
+    GP_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int user_chunk = lo.chunk;
     for (int kv : keys) {
         std::vector<CountJob> group;
         std::vector<int32_t> members;
         int64_t goff = 0;
+        // tasks per work-queue grab: the smallest any of the launch's jobs
+        // would take alone (a chunk sized by the whole batch's task count
+        // hands expensive tasks out in blocks of up to 64 and leaves long
+        // tails); about 64 grabs per warp of a 4-block-per-SM grid
+        int64_t chunk = 64;
         for (int32_t j = 0; j < njobs; ++j) {
             if (key[j] != kv) continue;
             group.push_back(jobs[j]);
             group.back().task_offset = goff;
             goff += jobs[j].nvirt;
             members.push_back(j);
+            chunk = std::min<int64_t>(chunk, jobs[j].nvirt / ((int64_t)nsm * 4 * 8 * 64));
         }
+        lo.chunk = user_chunk > 0 ? user_chunk : (int)std::max<int64_t>(1, chunk);
         std::vector<uint64_t> gres(2 * group.size(), 0);
         std::vector<int> gab(group.size(), 0);
         int64_t done = 0;
