@@ -12,11 +12,14 @@
 // Inside a task one warp runs the remaining loops depth-first. Candidate
 // sets are intersections of sorted neighbour lists, clipped to the window the
 // restrictions impose (a restriction becomes a bound on a sorted list, the
-// "break" of Section IV-B). An intersection iterates one list and tests each
-// element for membership in the other: with one bit probe when the other is
-// the neighbour list of a "core" vertex (the highest-degree vertices of a
+// "break" of Section IV-B). An intersection of lists of similar length is a
+// tile merge; otherwise it iterates the shorter list and tests each element
+// for membership in the other: with one bit probe when the other is the
+// neighbour list of a "core" vertex (the highest-degree vertices of a
 // degree-ordered graph, whose adjacency among themselves is kept as a bit
-// matrix), else with a binary search. Loops above the last two run one
+// matrix), else with a binary search. Plans switched to inclusion-exclusion
+// (Section IV-D) stop kk >= 2 loops early and add the number of distinct
+// kk-tuples from the inner candidate sets instead. Loops above the last two run one
 // candidate at a time with the whole warp cooperating on each intersection;
 // the loop at depth k-2 gives one candidate to each lane, which counts the
 // last level alone (heavy candidates go back to the whole warp). The last
