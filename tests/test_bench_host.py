@@ -26,3 +26,54 @@ def test_code_only_drops_comments_keeps_literals():
 def test_escaped_quote_inside_literal():
     b = bench()
     assert b._code_only('s = "a\\"b // c"; // d') == 's = "a\\"b // c";'
+
+
+def test_degree_strata_partition_the_degree_order():
+    """Strata of degree [2^i, 2^(i+1)) are contiguous id ranges of the
+    degree-ordered graph, in order, covering every non-isolated vertex."""
+    import numpy as np
+    import oracle
+    from synth import workload_edges
+    b = bench()
+    n, s, d = workload_edges("rmat12")
+    g, _ = oracle.degree_relabel(oracle.build_csr(n, s, d))
+    deg = np.diff(g.row_ptr)
+    strata = b.degree_strata(n, s, d)
+    assert strata[0][0] == 0
+    for (a0, b0, _), (a1, _, _) in zip(strata, strata[1:]):
+        assert b0 == a1
+    assert strata[-1][1] == int(np.count_nonzero(deg))
+    for a, e, lo in strata:
+        assert a < e and lo & (lo - 1) == 0
+        assert deg[a:e].min() >= lo and deg[a:e].max() < 2 * lo
+
+
+def test_task_sampler_is_stratified():
+    """One window per equal slice of the task space, inside its slice, all
+    windows disjoint and of the requested width; a space smaller than the
+    sample is taken whole."""
+    from paper_2009_10955_gb300.autotune import sample_ranges
+    nnz, windows, width = 1_000_003, 97, 50
+    r = sample_ranges(nnz, windows, width, seed=5)
+    step = nnz // windows
+    assert len(r) == windows
+    for i, (a, e) in enumerate(r):
+        assert e - a == width and i * step <= a and e <= (i + 1) * step
+    assert sample_ranges(100, 10, 20) == [(0, 100)]
+    assert sample_ranges(nnz, windows, width, seed=5) == r and sample_ranges(nnz, windows, width, seed=6) != r
+
+
+def test_busy_cycle_projection():
+    """The projection spreads a sample's busy warp cycles, scaled to all
+    tasks, over the launch's warps at the clock rate."""
+    from paper_2009_10955_gb300.autotune import project_s
+    assert project_s((2.07e9 * 1000, 1000), 10, 100) == 10.0
+    assert project_s((5, 0), 10, 100) is None and project_s((5, 8), 0, 100) is None
+
+
+def test_alu_peak_from_unit_counts():
+    b = bench()
+    peak, src = b.alu_peak_gops(152)
+    assert "152 SMs" in src
+    mhz = float(src.split(" MHz")[0].split("x")[-1])
+    assert abs(peak - 152 * 4 * 16 * mhz * 1e-3) < 1e-6
