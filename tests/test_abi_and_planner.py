@@ -190,6 +190,31 @@ def test_iep_form_of_top_plans(N, name):
     assert all(sc.iep(i) == (0, 1) for i in range(len(sc)))
 
 
+@pytest.mark.parametrize("name", ["c5", "house", "diamond", "tailed_triangle", "three_ears", "star5",
+                                  "path5", "grid3x2", "c6chord"])
+def test_iep_form_of_every_configuration(N, name):
+    """Sampled configurations (efficient schedule x Algorithm 1 set), not
+    only the model's top plans: the planner's kk and divisor equal the
+    definition's; a 5-cycle has no configuration with an inclusion-exclusion
+    form (every order with connected prefixes ends in an adjacent pair)."""
+    adj = named_pattern(name)
+    p = N.gp_pattern_create(adj)
+    scheds, _ = p.schedules()
+    sets = p.restriction_sets()
+    pairs = [(s, r) for s in scheds for r in sets]
+    step = max(1, len(pairs) // 60)
+    forms = []
+    for s, r in pairs[::step]:
+        sc = N.gp_schedule_explicit(p, s, r)
+        sc.set_iep(True)
+        forms.append(sc.iep(0))
+        assert forms[-1] == _iep_form(adj.tolist(), list(s), [tuple(x) for x in r]), (name, s, r)
+    if name == "c5":
+        assert all(f == (0, 1) for f in forms)
+    else:
+        assert any(f[0] >= 2 for f in forms)
+
+
 def test_labeled_pattern_groups(N):
     # equal labels give the plain group; alternating labels keep the
     # rotations by two and the reflections that fix the label classes;

@@ -52,7 +52,7 @@ def test_iep_every_configuration(env, pname):
         sc = N.gp_schedule_explicit(p, s, r)
         switched += sc.set_iep(True)
         assert N.gp_count(g, sc) == (N.GP_OK, expect), (s, r)
-    if pname != "c5":                 # c5 has no non-adjacent last pair in phase-1 orders? (any k'=1 pattern)
+    if pname != "c5":   # every connected-prefix order of C5 ends in an adjacent pair: no IEP form
         assert switched > 0
 
 
