@@ -36,7 +36,7 @@ def test_library_exports_every_declared_symbol(N):
 
 
 PATTERNS = ["triangle", "c4", "house", "k4", "c5", "diamond", "k6e", "c6chord", "grid3x2",
-            "tailed_triangle", "path4", "star4"]
+            "tailed_triangle", "path4", "star4", "star5", "c6"]
 
 
 @pytest.mark.parametrize("name", PATTERNS)
