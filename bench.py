@@ -645,7 +645,7 @@ def gpu_arm(a, rank, world):
                           "iep_loops": plans[p].iep(0)[0], "iep_divisor": plans[p].iep(0)[1],
                           "model_first": tuple(plans[p].get(0)[:2]) == model_pick[p]} for p in pats},
             "plan_choice": ("model's first plan" if a.model_plan else
-                            "fastest on a 128 x 64-task sample of the model's top 3 plans and their mirror "
+                            "fastest on a 256 x 64-task sample of the model's top 3 plans and their mirror "
                             "images (autotune.choose_plan), untimed"),
             "plan_candidates": plan_table,
             "graph_build_s": build_s,
