@@ -140,9 +140,12 @@ gp_status gp_pattern_aut_count(const gp_pattern* p, uint64_t* out);
 
 /* Restriction sets produced by Algorithm 1 (2-cycle based automorphism
  * elimination), each validated on the k-vertex complete graph. *count
- * receives how many there are (the search stops after `cap` sets, 0 = the
- * library's default cap). With pairs != NULL, set `idx` is written as
- * pairs[2r], pairs[2r+1] = (a, b) meaning id(a) > id(b), r < *n_pairs <= 21. */
+ * receives how many there are: the search stops after `cap` sets (0 = the
+ * default, 1024), and when it stops there the mirror image of every set
+ * found (each restriction reversed, also valid) is added, so up to 2 x cap.
+ * The sets of each cap are computed once per pattern. With pairs != NULL,
+ * set `idx` is written as pairs[2r], pairs[2r+1] = (a, b) meaning
+ * id(a) > id(b), r < *n_pairs <= 21. */
 gp_status gp_pattern_restriction_sets(gp_pattern* p, int32_t cap, int32_t* count,
                                       int32_t idx, int32_t* pairs, int32_t* n_pairs);
 

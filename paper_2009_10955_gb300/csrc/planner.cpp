@@ -201,7 +201,8 @@ bool validate_set(const PatternInfo& p, ResMask res) {
 const std::vector<ResMask>& restriction_sets(PatternInfo& p, int cap) {
     std::lock_guard<std::mutex> lock(p.mu);
     if (cap <= 0) cap = 1024;
-    if (p.sets_done && p.sets_cap == cap) return p.sets;
+    auto cached = p.sets.find(cap);
+    if (cached != p.sets.end()) return cached->second;
     const int k = p.k;
     const long n_orders = factorial(k);
     using Survivors = std::vector<uint16_t>;
@@ -272,11 +273,9 @@ const std::vector<ResMask>& restriction_sets(PatternInfo& p, int cap) {
         keyed.emplace_back(key, m);
     }
     std::sort(keyed.begin(), keyed.end());
-    p.sets.clear();
-    for (const auto& km : keyed) p.sets.push_back(km.second);
-    p.sets_done = true;
-    p.sets_cap = cap;
-    return p.sets;
+    std::vector<ResMask>& out = p.sets[cap];
+    for (const auto& km : keyed) out.push_back(km.second);
+    return out;
 }
 
 const std::vector<Perm>& efficient_schedules(PatternInfo& p, int* kprime) {

@@ -50,6 +50,25 @@ def test_planner_matches_oracle(N, name):
     assert sc == list(rsc) and kp == rkp
 
 
+def test_restriction_set_cap_and_mirrors(N):
+    """A capped search returns its sets plus their mirror images (every
+    restriction reversed), all valid; caps are cached side by side and the
+    default cap's sets do not change after a capped call."""
+    from math import factorial
+    adj = named_pattern("k5")
+    al = adj.tolist()
+    p = N.gp_pattern_create(adj)
+    full = p.restriction_sets()
+    small = p.restriction_sets(cap=8)
+    assert 8 <= len(small) <= 16 and len(full) == 2048
+    aut = len(pr.automorphisms(al))
+    for rs in small:
+        assert pr.validate(5, aut, set(rs))
+        assert tuple(sorted((b, a) for a, b in rs)) in {tuple(sorted(x)) for x in small}
+    assert p.restriction_sets() == full and p.restriction_sets(cap=8) == small
+    assert all(pr.linear_extensions(5, set(rs)) * aut == factorial(5) for rs in full[:64])
+
+
 @pytest.mark.parametrize("name", ["triangle", "house", "k4", "c5", "k6e", "grid3x2"])
 def test_cost_model_matches_oracle(N, name):
     adj = named_pattern(name)
