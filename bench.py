@@ -1,9 +1,11 @@
 #!/usr/bin/env python
 """Benchmark: pattern-count time on a device-resident synthetic graph.
 
-One step counts every pattern of the workload once with the plan the
-performance model ranks first (graph build and planning are excluded, as in
-the paper's evaluation; they appear in the end-to-end number instead).
+One step counts every pattern of the workload once with the plan chosen
+among the performance model's top plans and their mirror images by a task
+sample (--model-plan: the model's first); graph build and planning are
+excluded, as in the paper's evaluation, and appear in the end-to-end number
+instead.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat20]
   python bench.py --impl reference ...   # the CPU oracle on a bounded sample
@@ -29,6 +31,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2009_10955_gb300.shard import (allreduce_counts, graph_row_ptr, rank_tasks,  # noqa: E402,F401
+                                          shard_range, shard_roots)
 from synth import named_pattern, workload_edges  # noqa: E402
 
 WORKLOADS = {
@@ -287,43 +291,8 @@ def cpu_baseline(n, src, dst, patterns, budget_s, seed=12345, per_set=64):
 
 
 # ------------------------------------------------------- multi-rank helpers
-
-def shard_range(ntasks, rank, world):
-    """Contiguous share [lo, hi) of ntasks edge tasks for one rank."""
-    return ntasks * rank // world, ntasks * (rank + 1) // world
-
-
-def shard_roots(row_ptr, rank, world):
-    """Contiguous root range [lo, hi) of one rank, cut so that every rank gets
-    about the same estimated work: a root of degree d owns d edge tasks of
-    about d steps each, so a range weighs the sum of its roots' d^2. The
-    ranges partition the roots; a rank's weight exceeds the mean by at most
-    one root's."""
-    rp = np.asarray(row_ptr, dtype=np.int64)
-    deg = np.diff(rp).astype(np.float64)
-    cum = np.concatenate([[0.0], np.cumsum(deg * deg)])
-    n = len(rp) - 1
-
-    def cut(r):
-        if r <= 0:
-            return 0
-        if r >= world:
-            return n
-        return min(n, int(np.searchsorted(cum, cum[-1] * r / world, side="left")))
-    return cut(rank), cut(rank + 1)
-
-
-def allreduce_counts(counts, device=None):
-    """Exact sum over ranks of non-negative integer totals (< 2^128 each and
-    in total): each travels as four 32-bit limbs in int64 lanes, which cannot
-    overflow for fewer than 2^31 ranks."""
-    import torch
-    import torch.distributed as dist
-    limbs = torch.tensor([[(c >> (32 * i)) & 0xFFFFFFFF for i in range(4)] for c in counts],
-                         dtype=torch.int64, device=device)
-    dist.all_reduce(limbs)
-    return [sum(int(x) << (32 * i) for i, x in enumerate(row)) for row in limbs.tolist()]
-
+# the root partition and the exact 128-bit all-reduce live in the package
+# (paper_2009_10955_gb300/shard.py); the bench re-exports them
 
 # ------------------------------------------------------------------ GPU arm
 
@@ -426,9 +395,7 @@ def gpu_arm(a, rank, world):
     # this rank's share of every pattern's edge tasks: whole roots, balanced
     # by the sum of squared degrees
     if world > 1:
-        rp = g.csr()[0]
-        r0, r1 = shard_roots(rp, rank, world)
-        lo, hi = int(rp[r0]), int(rp[r1])
+        lo, hi = rank_tasks(graph_row_ptr(g), rank, world)
     else:
         lo, hi = 0, nnz
 
