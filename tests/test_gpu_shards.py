@@ -44,3 +44,21 @@ def test_shards_add_up(env, pname, iep, world):
         total += raw
     div = sc.iep(0)[1]
     assert total % div == 0 and total // div == whole
+
+
+@pytest.mark.parametrize("pname,iep", [("k4", False), ("house", True)])
+def test_package_rank_totals_add_up(env, pname, iep):
+    """The package's sharding layer (shard.rank_total over shard.graph_row_ptr,
+    as count_sharded runs it on each rank) on one GPU, rank after rank."""
+    from paper_2009_10955_gb300 import shard
+    N, g = env
+    sc = N.gp_schedule(N.gp_pattern_create(named_pattern(pname)), g)
+    if iep:
+        assert sc.set_iep(True) == 1
+    whole = N.gp_count(g, sc)[1]
+    rp = shard.graph_row_ptr(g)
+    assert (rp == g.csr()[0]).all()
+    for world in (1, 3):
+        total = sum(shard.rank_total(g, sc, 0, rank, world, row_ptr=rp) for rank in range(world))
+        assert shard.finish_count(total, sc.iep(0)[1]) == whole
+    assert shard.count_sharded(g, sc) == whole          # one process: every task on this rank
