@@ -266,3 +266,26 @@ def test_directed_patterns_host_side(N):
         with pytest.raises(N.GraphPiError) as e:
             N.gp_dpattern_create(bad)
         assert e.value.status == N.GP_ERR_PATTERN
+
+
+def test_plan_candidates_are_top_plans_and_mirrors(N):
+    """autotune.plan_candidates: the model's top plans in rank order, each
+    followed by its mirror image (every restriction reversed, a valid set of
+    the same model cost), no repeats."""
+    from paper_2009_10955_gb300 import autotune
+    for name in ("house", "k4", "k6e", "three_ears"):
+        adj = named_pattern(name)
+        p = N.gp_pattern_create(adj)
+        top = N.gp_schedule(p, None, top_k=3)
+        cands = autotune.plan_candidates(p, None, top_k=3)
+        assert len(set(cands)) == len(cands)
+        assert cands[0] == (top.get(0)[0], tuple(top.get(0)[1]))
+        aut = len(pr.automorphisms(adj.tolist()))
+        firsts = [(top.get(i)[0], tuple(top.get(i)[1])) for i in range(len(top))]
+        for order, res in cands:
+            mirror = tuple((b, a) for a, b in res)
+            assert (order, res) in firsts or (order, mirror) in firsts
+            assert pr.validate(len(adj), aut, set(res))
+            c = N.gp_config_cost(p, order, res, 2.0 ** 20, 8.0 * 2 ** 20, 6.0 * 8 * 2 ** 20)
+            m = N.gp_config_cost(p, order, mirror, 2.0 ** 20, 8.0 * 2 ** 20, 6.0 * 8 * 2 ** 20)
+            assert abs(c - m) <= 1e-12 * c
