@@ -42,3 +42,18 @@ def test_library_exports_no_oracle_symbol():
     path = lib._name
     syms = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
     assert "oracle" not in syms
+
+
+def test_no_cpu_fallback_without_a_device():
+    """Without a usable CUDA device the counting path fails loudly with
+    GP_ERR_CUDA; nothing is computed on the host instead."""
+    import numpy as np
+    import pytest
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_2009_10955_gb300 import native
+    N = native()
+    with pytest.raises(N.GraphPiError) as e:
+        N.gp_graph_create_edges(np.array([0, 1], np.int32), np.array([1, 2], np.int32), 3, N.GP_DEGREE_ORDER)
+    assert e.value.status == N.GP_ERR_CUDA
