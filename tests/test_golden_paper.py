@@ -77,3 +77,25 @@ def test_iep_count_equals_distinct_tuples(k):
         assert pr.iep_count(sets) == brute
         if k == 2:          # the form the count kernel evaluates
             assert brute == len(sets[0]) * len(sets[1]) - len(sets[0] & sets[1])
+
+
+def test_k7_automorphisms():
+    e = examples()["k7_automorphisms"]
+    adj = adj_from_edges(e["k"], [(a, b) for a in range(e["k"]) for b in range(a + 1, e["k"])])
+    assert oracle.aut_count(adj) == len(pr.automorphisms(adj.tolist())) == e["automorphisms"]
+
+
+def test_house_phase2():
+    e = examples()["house_phase2"]
+    adj = adj_from_edges(5, e["pattern_edges"]).tolist()
+    scheds, kp = pr.efficient_schedules(adj)
+    assert kp == e["phase2_k"] and scheds
+    assert all(not adj[s[-1]][s[-2]] for s in scheds)
+
+
+@pytest.mark.parametrize("V,E,T", [(1000.0, 5000.0, 12000.0), (2.0 ** 20, 8.0 * 2 ** 20, 6.0e9)])
+def test_cardinality_estimates(V, E, T):
+    examples()["cardinality_estimates"]
+    p1, p2 = pr.graph_params(V, E, T)
+    assert math.isclose(V * p1, 2.0 * E / V, rel_tol=1e-12)             # one neighbourhood
+    assert math.isclose(V * p1 * p2, T / (2.0 * E), rel_tol=1e-12)      # two adjacent vertices' lists
