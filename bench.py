@@ -79,9 +79,11 @@ def parse():
                     help="patterns outside the step: the device budget of their whole count")
     ap.add_argument("--batched-graph", default="rmat20",
                     help="graph of the batched comparison (64 random patterns x top-3 plans; '' to skip)")
-    ap.add_argument("--mode", default="count", choices=["count", "serve", "model", "case", "iep", "directed"],
+    ap.add_argument("--mode", default="count",
+                    choices=["count", "serve", "model", "case", "iep", "directed", "plan"],
                     help="serve: the continuous-batching sweep; model: performance-model accuracy; "
-                         "case: one untimed count of each pattern on --graph (for profiler captures)")
+                         "case: one untimed count of each pattern on --graph (for profiler captures); "
+                         "plan: host planning time of every named pattern (no GPU needed)")
     ap.add_argument("--graph", default="rmat16", help="synthetic graph of --mode case")
     ap.add_argument("--case-range", default="0,1",
                     help="--mode case: the fraction range [a, b) of the edge tasks to count")
@@ -967,6 +969,32 @@ def model_bench(N, stream, graph_name, patterns, max_configs=40, limit_s=5.0, ie
             "rows": rows}
 
 
+def plan_bench(repeats=3):
+    """Host planning time per named pattern (Section IV-A to IV-C: the
+    automorphisms, Algorithm 1's restriction sets, the efficient schedules
+    and the top-3 ranking by the performance model with default graph
+    statistics), best of `repeats` on a fresh pattern handle each time; the
+    counterpart of the paper's preprocessing times (Table III)."""
+    from paper_2009_10955_gb300 import native
+    from synth.patterns import NAMED_PATTERNS
+    N = native()
+    rows = {}
+    for name in NAMED_PATTERNS:
+        adj = named_pattern(name)
+        best = None
+        for _ in range(repeats):
+            t = time.perf_counter()
+            p = N.gp_pattern_create(adj)
+            sc = N.gp_schedule(p, None, top_k=3)
+            dt = time.perf_counter() - t
+            best = dt if best is None else min(best, dt)
+        rows[name] = {"k": int(adj.shape[0]), "aut": p.aut_count(), "restriction_sets": len(p.restriction_sets()),
+                      "schedules": len(p.schedules()[0]), "plans": len(sc), "plan_ms": best * 1000.0}
+    return {"metric": "host planning time (ms)", "unit": "ms", "cores": 1,
+            "host": os.uname().machine, "timing": f"best of {repeats}, fresh pattern handle each time",
+            "patterns": rows}
+
+
 def reference_arm(a):
     """The oracle on the host cores, each step a bounded random root sample."""
     wl = WORKLOADS[a.workload]
@@ -997,6 +1025,10 @@ def main():
     if a.impl == "reference":
         if rank == 0:
             print(json.dumps(reference_arm(a)), flush=True)
+        return
+    if a.mode == "plan":
+        if rank == 0:
+            print(json.dumps(plan_bench()), flush=True)
         return
     import torch
     if a.mode == "model":
