@@ -77,3 +77,18 @@ def test_alu_peak_from_unit_counts():
     assert "152 SMs" in src
     mhz = float(src.split(" MHz")[0].split("x")[-1])
     assert abs(peak - 152 * 4 * 16 * mhz * 1e-3) < 1e-6
+
+
+def test_plan_mode_covers_every_named_pattern():
+    """bench.py --mode plan (host planning time): one row per named pattern,
+    with the automorphism count of the oracle's planner restatement."""
+    from oracle import planner_ref as pr
+    from synth import named_pattern
+    from synth.patterns import NAMED_PATTERNS
+    out = bench().plan_bench(repeats=1)
+    assert set(out["patterns"]) == set(NAMED_PATTERNS)
+    for name, row in out["patterns"].items():
+        assert row["restriction_sets"] > 0 and row["schedules"] > 0 and row["plans"] >= 1
+        assert row["plan_ms"] >= 0.0
+        if row["k"] <= 6:
+            assert row["aut"] == len(pr.automorphisms(named_pattern(name).tolist()))
