@@ -137,8 +137,7 @@ bool no_conflict(const Perm& perm, ResMask res, int k) {
 namespace {
 
 // Number of the k! relative orders of the pattern vertices that obey res.
-long linear_extensions(int k, ResMask res) {
-    const OrderTable& t = order_table(k);
+long linear_extensions(const OrderTable& t, ResMask res) {
     uint64_t alive[kMaxOrderWords];
     for (int w = 0; w < t.words; ++w) alive[w] = ~0ull;
     if (t.n % 64) alive[t.words - 1] = (1ull << (t.n % 64)) - 1;
@@ -185,7 +184,7 @@ private:
 }  // namespace
 
 bool validate_set(const PatternInfo& p, ResMask res) {
-    return linear_extensions(p.k, res) * (long)p.auts.size() == (long)factorial(p.k);
+    return linear_extensions(order_table(p.k), res) * (long)p.auts.size() == (long)factorial(p.k);
 }
 
 // Algorithm 1. generate(pg, res_set) depends only on res_set: pg is exactly
@@ -205,6 +204,7 @@ const std::vector<ResMask>& restriction_sets(PatternInfo& p, int cap) {
     if (cached != p.sets.end()) return cached->second;
     const int k = p.k;
     const long n_orders = factorial(k);
+    const OrderTable& orders = order_table(k);
     using Survivors = std::vector<uint16_t>;
     MaskSet visited;
     std::unordered_set<ResMask> found;
@@ -219,7 +219,7 @@ const std::vector<ResMask>& restriction_sets(PatternInfo& p, int cap) {
         stack.pop_back();
         // restrictions only ever remove orders: a set that already obeys
         // fewer than k!/|Aut| of them has no valid set below it
-        const long ext_aut = linear_extensions(k, rs) * (long)p.auts.size();
+        const long ext_aut = linear_extensions(orders, rs) * (long)p.auts.size();
         if (ext_aut < n_orders) continue;
         auto pg = std::make_shared<Survivors>();
         for (uint16_t i : *parent)
@@ -431,7 +431,7 @@ bool compile_plan(const PatternInfo& p, const int8_t* sched, ResMask res, GpPlan
     plan.lvl[0].src_kind = 0;
     for (int x = 1; x < k; ++x) {
         GpLevel& L = plan.lvl[x];
-        int ops[GP_MAX_K], nops = 0;
+        int ops[GP_MAX_K] = {}, nops = 0;
         uint8_t lo = 0, hi = 0, opmask = 0;
         for (int j = 0; j < x; ++j) {
             if (p.adj[sched[x]][sched[j]]) { ops[nops++] = j; opmask |= (uint8_t)(1u << j); }
