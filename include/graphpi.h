@@ -143,7 +143,9 @@ gp_status gp_pattern_aut_count(const gp_pattern* p, uint64_t* out);
  * receives how many there are: the search stops after `cap` sets (0 = the
  * default, 1024), and when it stops there the mirror image of every set
  * found (each restriction reversed, also valid) is added, so up to 2 x cap.
- * The sets of each cap are computed once per pattern. With pairs != NULL,
+ * The pattern caches the sets of the last cap asked for (gp_schedule asks
+ * for the default); asking for another cap recomputes them, so such a call
+ * must not overlap another call on the same pattern. With pairs != NULL,
  * set `idx` is written as pairs[2r], pairs[2r+1] = (a, b) meaning
  * id(a) > id(b), r < *n_pairs <= 21. */
 gp_status gp_pattern_restriction_sets(gp_pattern* p, int32_t cap, int32_t* count,

@@ -64,9 +64,6 @@ const OrderTable& order_table(int k) {
     return *tables[k];
 }
 
-// 64-bit words of a set of k! relative orders, k <= GP_MAX_K
-constexpr int kMaxOrderWords = (5040 + 63) / 64;
-
 int popcount_words(const uint64_t* w, int n) {
     int c = 0;
     for (int i = 0; i < n; ++i) c += __builtin_popcountll(w[i]);
@@ -134,114 +131,51 @@ bool no_conflict(const Perm& perm, ResMask res, int k) {
     return acyclic(out, k);
 }
 
-namespace {
-
-// Number of the k! relative orders of the pattern vertices that obey res.
-long linear_extensions(const OrderTable& t, ResMask res) {
-    uint64_t alive[kMaxOrderWords];
-    for (int w = 0; w < t.words; ++w) alive[w] = ~0ull;
-    if (t.n % 64) alive[t.words - 1] = (1ull << (t.n % 64)) - 1;
+bool validate_set(const PatternInfo& p, ResMask res) {
+    const OrderTable& t = order_table(p.k);
+    std::vector<uint64_t> alive((size_t)t.words, ~0ull);
+    if (t.n % 64) alive.back() = (1ull << (t.n % 64)) - 1;
     for (ResMask m = res; m; m &= m - 1) {
         int bit = __builtin_ctzll(m);
         const uint64_t* g = t.pair(bit / GP_MAX_K, bit % GP_MAX_K);
         for (int w = 0; w < t.words; ++w) alive[w] &= g[w];
     }
-    return popcount_words(alive, t.words);
-}
-
-// Open-addressing hash set of restriction masks (no mask has bit 63 set,
-// so ~0 marks an empty slot).
-class MaskSet {
-public:
-    bool insert(ResMask m) {
-        if (2 * (n_ + 1) > slots_.size()) grow();
-        size_t i = slot(m);
-        if (slots_[i] == m) return false;
-        slots_[i] = m;
-        ++n_;
-        return true;
-    }
-    size_t size() const { return n_; }
-
-private:
-    static constexpr ResMask kEmpty = ~0ull;
-    std::vector<ResMask> slots_ = std::vector<ResMask>(1024, kEmpty);
-    size_t n_ = 0;
-    size_t slot(ResMask m) const {
-        size_t mask = slots_.size() - 1;
-        size_t i = (size_t)((m * 0x9E3779B97F4A7C15ull) >> 20) & mask;
-        while (slots_[i] != kEmpty && slots_[i] != m) i = (i + 1) & mask;
-        return i;
-    }
-    void grow() {
-        std::vector<ResMask> old(slots_.size() * 2, kEmpty);
-        old.swap(slots_);
-        for (ResMask m : old)
-            if (m != kEmpty) slots_[slot(m)] = m;
-    }
-};
-
-}  // namespace
-
-bool validate_set(const PatternInfo& p, ResMask res) {
-    return linear_extensions(order_table(p.k), res) * (long)p.auts.size() == (long)factorial(p.k);
+    long ext = popcount_words(alive.data(), t.words);
+    return ext * (long)p.auts.size() == (long)t.n;
 }
 
 // Algorithm 1. generate(pg, res_set) depends only on res_set: pg is exactly
 // the automorphisms that no_conflict keeps under res_set, because a
 // permutation that closes a cycle under a set also closes it under every
 // superset. Each set is therefore explored once, and every validated leaf is
-// added to one global result set. The same monotonicity lets a set test only
-// the automorphisms its parent kept (each stack entry carries the parent's
-// survivors, shared among siblings), and a set obeyed by fewer than
-// k!/|Aut| relative orders is dropped with everything below it, since
-// validate needs exactly that many. Neither changes which sets are found
-// or in which order.
+// added to one global result set.
 const std::vector<ResMask>& restriction_sets(PatternInfo& p, int cap) {
     std::lock_guard<std::mutex> lock(p.mu);
     if (cap <= 0) cap = 1024;
-    auto cached = p.sets.find(cap);
-    if (cached != p.sets.end()) return cached->second;
+    if (p.sets_done && p.sets_cap == cap) return p.sets;
     const int k = p.k;
-    const long n_orders = factorial(k);
-    const OrderTable& orders = order_table(k);
-    using Survivors = std::vector<uint16_t>;
-    MaskSet visited;
-    std::unordered_set<ResMask> found;
+    std::unordered_set<ResMask> visited, found;
     const size_t visit_cap = (size_t)1 << 21;
-    auto all = std::make_shared<Survivors>(p.auts.size());
-    for (size_t i = 0; i < p.auts.size(); ++i) (*all)[i] = (uint16_t)i;
-    std::vector<std::pair<ResMask, std::shared_ptr<const Survivors>>> stack{{0, all}};
+    std::vector<ResMask> stack{0};
     visited.insert(0);
     while (!stack.empty() && found.size() < (size_t)cap && visited.size() < visit_cap) {
-        ResMask rs = stack.back().first;
-        std::shared_ptr<const Survivors> parent = std::move(stack.back().second);
+        ResMask rs = stack.back();
         stack.pop_back();
-        // restrictions only ever remove orders: a set that already obeys
-        // fewer than k!/|Aut| of them has no valid set below it
-        const long ext_aut = linear_extensions(orders, rs) * (long)p.auts.size();
-        if (ext_aut < n_orders) continue;
-        auto pg = std::make_shared<Survivors>();
-        for (uint16_t i : *parent)
-            if (no_conflict(p.auts[i], rs, k)) pg->push_back(i);
-        parent.reset();
-        if (pg->size() > 1) {
+        std::vector<const Perm*> pg;
+        for (const Perm& q : p.auts)
+            if (no_conflict(q, rs, k)) pg.push_back(&q);
+        if (pg.size() > 1) {
             // pairs (a, b) with a < b are pushed last and so explored first
-            for (uint16_t i : *pg) {
-                const Perm& q = p.auts[i];
+            for (const Perm* q : pg)
                 for (int v = k - 1; v >= 0; --v) {
-                    int w = q[v];
-                    if (w == v || q[w] != v) continue;       // not a 2-cycle (v, w)
-                    // already in the set, or its reverse is: a set holding
-                    // both orientations of a pair orders nothing and can
-                    // neither validate nor have children
-                    if ((rs >> res_bit(v, w) | rs >> res_bit(w, v)) & 1) continue;
-                    ResMask ns = rs | (1ull << res_bit(v, w));
-                    if (visited.insert(ns)) stack.emplace_back(ns, pg);
+                    int w = (*q)[v];
+                    if (w != v && (*q)[w] == v) {           // a 2-cycle (v, w)
+                        ResMask ns = rs | (1ull << res_bit(v, w));
+                        if (visited.insert(ns).second) stack.push_back(ns);
+                    }
                 }
-            }
-        } else {
-            if (ext_aut == n_orders) found.insert(rs);        // validate
+        } else if (validate_set(p, rs)) {
+            found.insert(rs);
         }
     }
     // Reversing every restriction of a valid set gives a valid set with the
@@ -260,22 +194,19 @@ const std::vector<ResMask>& restriction_sets(PatternInfo& p, int cap) {
         }
         for (ResMask r : mirrors) found.insert(r);
     }
+    p.sets.assign(found.begin(), found.end());
     // deterministic order: by the sorted list of pairs, as (a, b) tuples
-    // (a shorter list before its extensions: 1 + 16a + b, padded with 0)
-    using Key = std::array<uint8_t, GP_MAX_K * GP_MAX_K + 1>;
-    std::vector<std::pair<Key, ResMask>> keyed;
-    for (ResMask m : found) {
-        Key key{};
-        int n = 0;
+    auto key = [k](ResMask m) {
+        std::vector<int> v;
         for (int a = 0; a < k; ++a)
             for (int b = 0; b < k; ++b)
-                if (m >> res_bit(a, b) & 1) key[n++] = (uint8_t)(1 + a * 16 + b);
-        keyed.emplace_back(key, m);
-    }
-    std::sort(keyed.begin(), keyed.end());
-    std::vector<ResMask>& out = p.sets[cap];
-    for (const auto& km : keyed) out.push_back(km.second);
-    return out;
+                if (m >> res_bit(a, b) & 1) v.push_back(a * 16 + b);
+        return v;
+    };
+    std::sort(p.sets.begin(), p.sets.end(), [&](ResMask x, ResMask y) { return key(x) < key(y); });
+    p.sets_done = true;
+    p.sets_cap = cap;
+    return p.sets;
 }
 
 const std::vector<Perm>& efficient_schedules(PatternInfo& p, int* kprime) {
@@ -431,7 +362,7 @@ bool compile_plan(const PatternInfo& p, const int8_t* sched, ResMask res, GpPlan
     plan.lvl[0].src_kind = 0;
     for (int x = 1; x < k; ++x) {
         GpLevel& L = plan.lvl[x];
-        int ops[GP_MAX_K] = {}, nops = 0;
+        int ops[GP_MAX_K], nops = 0;
         uint8_t lo = 0, hi = 0, opmask = 0;
         for (int j = 0; j < x; ++j) {
             if (p.adj[sched[x]][sched[j]]) { ops[nops++] = j; opmask |= (uint8_t)(1u << j); }

@@ -3,7 +3,6 @@
 // the GpPlan that the counting kernel interprets.
 #pragma once
 #include <array>
-#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -27,9 +26,9 @@ struct PatternInfo {
     std::vector<Perm> auts;          // automorphism group (Section IV-A)
 
     std::mutex mu;                   // guards the lazily computed members below
-    // Algorithm 1 output per search cap; map nodes never move, so a
-    // returned reference stays valid while other caps are added
-    std::map<int, std::vector<ResMask>> sets;
+    bool sets_done = false;
+    int sets_cap = 0;
+    std::vector<ResMask> sets;       // Algorithm 1 output
     bool scheds_done = false;
     int kprime = 0;
     std::vector<Perm> scheds;        // efficient schedules (Section IV-B)
@@ -41,8 +40,7 @@ bool pattern_init(PatternInfo& p, const uint8_t* adj, int k, std::string& err);
 // Same for a vertex-labelled pattern: automorphisms must also preserve labels.
 bool pattern_init_labeled(PatternInfo& p, const uint8_t* adj, const int32_t* labels, int k, std::string& err);
 
-// Algorithm 1 restriction sets (cached on the pattern per cap; the
-// reference stays valid for the pattern's lifetime). cap <= 0: default.
+// Algorithm 1 restriction sets (cached on the pattern). cap <= 0: default.
 const std::vector<ResMask>& restriction_sets(PatternInfo& p, int cap);
 
 // Efficient schedules, 2-phase filter with phase 2 relaxed (cached).
