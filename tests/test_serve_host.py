@@ -277,3 +277,50 @@ def test_latency_runs_from_arrival_and_planning_does_not_block_submit(fake):
     assert lat[-1] >= 0.6
     assert given.arrival == t0 and given.latency >= 0.8
     assert [r.count for r in reqs] == [30, 40, 50, 60]
+
+
+class FakeIepSched(FakeSched):
+    """An inclusion-exclusion plan: a 4-vertex pattern divides by 2, a
+    5-vertex one by 3 (its fake totals are then not divisible)."""
+
+    def set_iep(self, enable=True):
+        return 1
+
+    def iep(self, idx=0):
+        return (2, 2) if self.k == 4 else (2, 3) if self.k == 5 else (0, 1)
+
+
+class FakeIepNative(FakeNative):
+    """Slices return undivided 128-bit totals: (tasks x k) x 2 for every
+    plan, and 2^64 per task on top for 6-vertex patterns, whose counts then
+    need more than 64 bits."""
+
+    def gp_schedule(self, pattern, graph, top_k=1, stream=None):
+        return FakeIepSched(pattern)
+
+    def gp_count_batch_ranges(self, graphs, scheds, idx, begin, end, opts, stream=None, raw=None):
+        st, out, nxt = self._ranges(scheds, begin, end)
+        assert raw is not None
+        for j, (s, b, t) in enumerate(zip(scheds, begin, nxt)):
+            total = int(out[j]) * 2 + ((int(t) - b) << 64 if s.k == 6 else 0)
+            raw[2 * j], raw[2 * j + 1] = total & ((1 << 64) - 1), total >> 64
+            out[j] = 0                                  # partial IEP totals are not counts
+        return st, out, nxt
+
+
+def test_inclusion_exclusion_totals_divided_once(monkeypatch):
+    f = FakeIepNative(per_slice=7)
+    monkeypatch.setattr(serve, "N", f)
+    srv = serve.Server({"a": FakeGraph(100)}, slice_ms=1.0, iep=True)
+    try:
+        reqs = [srv.submit("a", adj_k(k)) for k in (3, 4, 5, 6)]
+        wait_all(reqs)
+    finally:
+        srv.close()
+    # 3 vertices: divisor 1, raw = 2 x count of the fake; 4: divisor 2
+    assert reqs[0].count == 600 and reqs[0].error is None
+    assert reqs[1].count == 400 and reqs[1].error is None
+    # 5 vertices: 100 x 5 x 2 = 1000 is not a multiple of 3; 6: beyond 64 bits
+    assert reqs[2].count is None and isinstance(reqs[2].error, ArithmeticError)
+    assert reqs[3].count is None and isinstance(reqs[3].error, ArithmeticError)
+    assert reqs[1].slices == 15
