@@ -5,7 +5,6 @@ the same task sample; the one with the smallest busy-cycle projection wins,
 a candidate whose sample launch stopped early is dropped, and the choice is
 cached per graph and pattern."""
 
-import ctypes
 import json
 
 import numpy as np
