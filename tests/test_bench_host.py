@@ -92,3 +92,26 @@ def test_plan_mode_covers_every_named_pattern():
         assert row["plan_ms"] >= 0.0
         if row["k"] <= 6:
             assert row["aut"] == len(pr.automorphisms(named_pattern(name).tolist()))
+
+
+def test_clock_sampler_summary():
+    """The clocks record of the line: median SM clock under load, the maximum,
+    and every throttle reason seen active in any sample."""
+    b = bench()
+
+    class FakeProc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    cs = object.__new__(b.ClockSampler)
+    cs.proc, cs.uuid = FakeProc(), "GPU-fake"
+    cs.rows = [["2070", "2070", "900.5", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
+               ["1965", "2070", "1390.0", "0x4", "Not Active", "Not Active", "Not Active", "Active"],
+               ["2070", "2070", "1000.0", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
+               ["[N/A]", "2070", "1000.0", "0x0", "Not Active", "Active", "Not Active", "Not Active"]]
+    out = cs.stop()
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 4
+    assert out["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
