@@ -28,7 +28,9 @@
  *    matching *_destroy call (NULL is accepted and ignored). Handles are
  *    read-only after creation and may be shared between threads and
  *    streams, except that a graph must not be destroyed while a count on it
- *    is in flight.
+ *    is in flight, and that gp_schedule_set_iep, gp_graph_set_labels and a
+ *    gp_pattern_restriction_sets call with another cap change their handle
+ *    (each documents it).
  *  - Streams: a `void* stream` is a cudaStream_t (NULL = the legacy default
  *    stream). Device work runs on that stream. Every call documents whether
  *    it synchronises the stream before returning.
@@ -132,7 +134,8 @@ gp_status gp_pattern_create_labeled(const uint8_t* adj, const int32_t* labels, i
 
 /* Attach vertex labels to a graph: labels (host) has n entries in the
  * labelling of the input pairs (the library applies its degree relabel).
- * Replaces earlier labels. Synchronous. */
+ * Replaces earlier labels, so it must not overlap a count on g.
+ * Synchronous. */
 gp_status gp_graph_set_labels(gp_graph* g, const int32_t* labels, void* stream);
 
 /* |Aut(P)|: permutations of V_p that preserve E_p. */
@@ -198,7 +201,9 @@ gp_status gp_schedule_explicit(const gp_pattern* p, const int32_t* order, const 
  * in gp_count_opts.raw_total; totals of disjoint ranges add up, and their
  * sum divided by the plan's divisor (gp_schedule_iep) is the count. With
  * kk = 5 the graph's maximum degree must be below 2^24 (GP_ERR_ARG
- * otherwise), so that every term stays inside 128 bits. */
+ * otherwise), so that every term stays inside 128 bits. This call changes
+ * the handle (the one exception to read-only handles): it must not overlap
+ * another call that uses s. */
 gp_status gp_schedule_set_iep(gp_schedules* s, int32_t enable, int32_t* n_iep);
 
 /* Inclusion-exclusion form of plan idx: *kk (may be NULL) receives the
