@@ -8,8 +8,9 @@ import re
 import numpy as np
 import pytest
 
+import oracle
 from oracle import planner_ref as pr
-from synth import named_pattern, random_pattern_set
+from synth import er_edges, named_pattern, random_pattern_set
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -289,3 +290,27 @@ def test_plan_candidates_are_top_plans_and_mirrors(N):
             c = N.gp_config_cost(p, order, res, 2.0 ** 20, 8.0 * 2 ** 20, 6.0 * 8 * 2 ** 20)
             m = N.gp_config_cost(p, order, mirror, 2.0 ** 20, 8.0 * 2 ** 20, 6.0 * 8 * 2 ** 20)
             assert abs(c - m) <= 1e-12 * c
+
+
+@pytest.mark.parametrize("name", ["c7", "k7", "star7"])
+def test_seven_vertex_sets_are_valid(N, name):
+    """7-vertex patterns, whose full restriction-set search the oracle's
+    restatement cannot finish quickly: every library set passes validate
+    (Section IV-A), mirror images come in pairs, and on a small graph a
+    sample of the sets times |Aut| gives the unrestricted map count."""
+    adj = named_pattern(name)
+    al = adj.tolist()
+    p = N.gp_pattern_create(adj)
+    aut = len(pr.automorphisms(al))
+    assert p.aut_count() == aut
+    sets = p.restriction_sets()
+    keyed = {tuple(sorted(r)) for r in sets}
+    for r in sets:
+        assert pr.validate(7, aut, set(r))
+        assert tuple(sorted((b, a) for a, b in r)) in keyed
+    s, d = er_edges(14, 60, seed=3)
+    g = oracle.build_csr(14, s, d)
+    maps = oracle.count_maps(adj, g)
+    sched = p.schedules()[0][0]
+    for r in sets[:: max(1, len(sets) // 6)]:
+        assert oracle.count_restricted(adj, sched, r, g) * aut == maps, r
