@@ -14,12 +14,17 @@ model from the paper's definitions.
   them; an embedding sends every pattern arc to a graph arc).
 * ``planner_ref.py`` (plain Python): automorphisms, Algorithm 1 with
   ``no_conflict`` and ``validate``, the 2-phase schedule filter and the
-  performance model (Sections IV-A to IV-C).
+  performance model (Sections IV-A to IV-C), Algorithm 2 and the
+  inclusion-exclusion count of distinct tuples (Section IV-D).
+* ``iep_total`` (here): a whole count with the innermost loops replaced by
+  that inclusion-exclusion count (Section IV-D), on small graphs.
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``,
-``tests/test_oracle_pins_directed.py`` and ``tests/test_golden_paper.py``
-(closed forms, brute force over vertex tuples, values the paper prints); the
-mutation tests show that the pins catch planted mistakes.
+``tests/test_oracle_pins_directed.py``, ``tests/test_golden_paper.py``,
+``tests/test_cost_pins.py``, ``tests/test_iep_divisor.py`` and
+``tests/test_iep_partitions.py`` (closed forms, brute force over vertex
+tuples, values the paper prints); the mutation tests show that the pins
+catch planted mistakes.
 """
 
 import ctypes
