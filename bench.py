@@ -357,6 +357,16 @@ def phase(name):
     print(f"[bench {time.time() - _T0:7.1f} s] {name}", file=sys.stderr, flush=True)
 
 
+def workload_config(workload, graph, n, m_undirected, max_deg, patterns):
+    """The `config` of both benchmark arms: what the workload is (graph,
+    its size, the patterns of one step) and how L2 is treated between timed
+    GPU counts. Run results and the method's choices go elsewhere in the
+    line, so the two arms report one identical config."""
+    return {"workload": workload, "graph": graph, "n": int(n), "m_undirected": int(m_undirected),
+            "max_deg": int(max_deg), "patterns": list(patterns),
+            "l2": "GPU counts: L2 flushed (512 MB write) before every count"}
+
+
 def gpu_arm(a, rank, world):
     import torch
     import torch.distributed as dist
@@ -603,11 +613,8 @@ def gpu_arm(a, rank, world):
         "vs_baseline": None,
         "dtype": "int32",
         "data": "synthetic",
-        "config": {
-            "workload": a.workload,
-            "graph": wl["graph"],
-            "n": st["n"], "m_undirected": st["m"], "max_deg": st["max_deg"],
-            "patterns": pats,
+        "config": workload_config(a.workload, wl["graph"], st["n"], st["m"], st["max_deg"], pats),
+        "results": {
             "counts": {p: counts[p] for p in pats},
             "per_pattern_s": {p: mean_kern[p] / 1000.0 for p in pats},
             "plans": {p: {"order": plans[p].get(0)[0], "restrictions": plans[p].get(0)[1],
@@ -621,10 +628,9 @@ def gpu_arm(a, rank, world):
             "plan_s": plan_s,
             "tuned": tuned,
             "tune_s": tune_s,
-            "l2": "flushed (512 MB write) before every count",
-            "step": "one count of each pattern, device-resident graph",
-            "parallelism": f"edge tasks sharded over {world} GPU(s)",
         },
+        "method": {"step": "one count of each pattern, device-resident graph",
+                   "parallelism": f"edge tasks sharded over {world} GPU(s)"},
         "e2e": {"value": statistics.mean(e2e_ms) / 1000.0, "unit": "s",
                 "h2d_bytes_per_step": int(src.nbytes + dst.nbytes),
                 "d2h_bytes_per_step": 16 * len(pats),
@@ -1000,6 +1006,12 @@ def reference_arm(a):
     wl = WORKLOADS[a.workload]
     pats = a.patterns.split(",") if a.patterns else wl["patterns"]
     n, src, dst = workload_edges(wl["graph"])
+    import oracle
+    ref = oracle.build_csr(n, src, dst)
+    deg = np.diff(ref.row_ptr)
+    config = workload_config(a.workload, wl["graph"], n, int(ref.row_ptr[-1]) // 2,
+                             int(deg.max()) if n else 0, pats)
+    del ref, deg
     per_step = max(2.0, 150.0 / max(1, a.steps + a.warmup))
     vals = []
     cb = None
@@ -1012,7 +1024,9 @@ def reference_arm(a):
     return {"metric": "pattern-count time (s)", "value": v, "unit": "s", "n_gpus": a.gpus, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": v * 1000.0, "higher_is_better": False, "impl": "reference",
             "scaling": "strong", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": a.workload, "graph": wl["graph"], "patterns": pats},
+            "config": config,
+            "method": {"step": "one bounded, degree-stratified root sample of each pattern",
+                       "parallelism": "host cores (the oracle runs on the CPU; rank 0 alone)"},
             "devices": "host cores only (the oracle runs on the CPU; rank 0 alone)",
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

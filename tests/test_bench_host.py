@@ -115,3 +115,23 @@ def test_clock_sampler_summary():
     out = cs.stop()
     assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 4
     assert out["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+
+
+def test_both_arms_report_one_config():
+    """The reference arm's config is the workload's, built by the same
+    function the GPU arm uses, with sizes from the oracle's CSR of the same
+    pairs (which the GPU graph build matches bit for bit)."""
+    import argparse
+    import oracle
+    from synth import workload_edges
+    import bench as b                 # importable by name: the oracle runs in spawned children
+    a = argparse.Namespace(workload="er2000", patterns=None, steps=1, warmup=0, gpus=1)
+    out = b.reference_arm(a)
+    n, s, d = workload_edges("er2000")
+    g = oracle.build_csr(n, s, d)
+    import numpy as np
+    expect = b.workload_config("er2000", "er2000", n, int(g.row_ptr[-1]) // 2, int(np.diff(g.row_ptr).max()),
+                               ["house"])
+    assert out["config"] == expect
+    assert set(expect) == {"workload", "graph", "n", "m_undirected", "max_deg", "patterns", "l2"}
+    assert out["impl"] == "reference" and out["e2e"]["value"] == out["value"]
