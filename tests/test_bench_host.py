@@ -135,3 +135,18 @@ def test_both_arms_report_one_config():
     assert out["config"] == expect
     assert set(expect) == {"workload", "graph", "n", "m_undirected", "max_deg", "patterns", "l2"}
     assert out["impl"] == "reference" and out["e2e"]["value"] == out["value"]
+
+
+def test_driver_command_lines_parse(monkeypatch):
+    """The command lines the benchmark is launched with parse, with N = 1
+    and a few-minute run as the defaults."""
+    import sys
+    b = bench()
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    a = b.parse()
+    assert (a.gpus, a.impl, a.workload, a.mode) == (1, "gb300", "rmat20", "count") and a.warmup >= 3
+    for argv in (["--gpus", "1", "--steps", "20", "--warmup", "5"],
+                 ["--impl", "reference", "--gpus", "2", "--steps", "20", "--warmup", "5"],
+                 ["--workload", "cl4m", "--steps", "2"], ["--mode", "plan"], ["--mode", "iep"]):
+        monkeypatch.setattr(sys, "argv", ["bench.py"] + argv)
+        b.parse()
