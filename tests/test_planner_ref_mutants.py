@@ -7,7 +7,6 @@ with the real functions. CPU only."""
 import itertools
 from math import factorial
 
-import numpy as np
 import pytest
 
 import oracle
