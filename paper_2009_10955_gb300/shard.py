@@ -13,7 +13,6 @@ The partition and the reduction are host logic; every count runs in the
 library's kernels.
 """
 
-
 import numpy as np
 
 from . import _native as N
